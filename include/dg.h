@@ -1,0 +1,213 @@
+/*
+ * dg.h -- C ABI of the GB300 matrix-free modal DG + p-multigrid FGMRES library.
+ *
+ * Method: Franciolini, Fidkowski & Crivellini, "Efficient discontinuous Galerkin
+ * implementations and preconditioners for implicit unsteady compressible flow
+ * simulations" (arXiv 1812.04789).  Every entry point cites the passage that
+ * defines the operation it computes.
+ *
+ * Conventions for every call
+ *  - Pointers named as device pointers are CUDA device memory owned by the
+ *    caller, contiguous, FP64, laid out W[e][v][i]: element e (e = i0 + n0*(i1 +
+ *    n1*i2)), conservative variable v = 0..m-1 (rho, rho*v_1..rho*v_d, rho*e0;
+ *    m = d + 2), modal coefficient i = 0..n_m-1 of the orthonormal total-degree
+ *    Legendre basis ordered by degree, then lexicographically with the first
+ *    index descending.  n_m = C(p + d, d).
+ *  - Host pointers (descriptors, options, statistics) are read or written
+ *    during the call only; the library keeps no reference to them.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *  - The return value reports argument validation and launch errors at call
+ *    time.  Outcomes found on the device (non-physical states, Krylov
+ *    breakdown) are recorded in a per-mesh device status word read by
+ *    dg_status_sync(), and by dg_fgmres_step() in its statistics.
+ *  - Handles own their device workspace (basis tables, face slots, blocks,
+ *    Krylov bases); it is allocated by the create/setup calls, never during
+ *    residual, JVP, apply or solve calls.  A handle is not safe for concurrent
+ *    use from several host threads or several streams at once.
+ *  - There is no CPU fallback: without a CUDA device every call returns
+ *    DG_ERR_CUDA.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_INVALID = 1,        /* bad argument: null handle/pointer, bad size or option */
+  DG_ERR_OOM = 2,            /* device allocation failed in a create/setup call */
+  DG_ERR_CUDA = 3,           /* a CUDA runtime call or kernel launch failed */
+  DG_ERR_NONPHYSICAL = 4,    /* rho <= 0 or p <= 0 met at a quadrature point */
+  DG_ERR_NOT_CONVERGED = 5,  /* FGMRES stopped at its iteration limit above tolerance */
+  DG_ERR_BREAKDOWN = 6,      /* singular element block, or non-finite Krylov scalar */
+  DG_ERR_TIMEOUT = 7,        /* a bounded device wait ran out */
+  DG_ERR_UNSUPPORTED = 8     /* valid request this build does not implement */
+} dg_status;
+
+/* Periodic structured mesh of boxes on [lo, hi] (quads for dim 2, hexes for
+ * dim 3) with n[k] elements per direction, polynomial degree p (0..8) and nq1d
+ * Gauss-Legendre points per direction on volumes and faces (0 => p + 2).
+ * Sec. 3 (broken space, eq. BSpace) and Sec. 3.1 (DG discretisation). */
+typedef struct {
+  int dim;
+  int n[3];
+  double lo[3], hi[3];
+  int p;
+  int nq1d;
+} dg_mesh_desc;
+
+/* Gas and discretisation constants (Sec. 2 closure; Sec. 3.1): ratio of specific
+ * heats, Prandtl number, constant viscosity, gas constant, BR2 penalty eta_F
+ * (must exceed the number of element faces; 0 => 2*dim + 1) and the Roe
+ * entropy-fix fraction (|lambda| smoothed below roe_delta * c; 0 = plain Roe). */
+typedef struct {
+  double gamma, Pr, mu, Rgas, eta_br2, roe_delta;
+} dg_physics;
+
+typedef struct dg_mesh_s* dg_mesh;
+typedef struct dg_pmg_s* dg_pmg;
+
+/* Build the mesh handle: face-neighbour maps, basis/quadrature tables in FP64
+ * and FP32 on the device, face-slot workspace.  Blocks until the tables are
+ * uploaded.  Errors: DG_ERR_INVALID (dim not 2/3, n < 1, p out of range,
+ * hi <= lo, nq1d < p + 1), DG_ERR_OOM, DG_ERR_CUDA.  *out is NULL on error. */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_physics* phys, void* stream,
+                         dg_mesh* out);
+dg_status dg_mesh_destroy(dg_mesh mesh);
+
+/* Sizes: elements, modes per variable, variables (m), total DOFs E*m*n_m. */
+dg_status dg_mesh_info(dg_mesh mesh, int* n_elem, int* n_modes, int* n_vars, size_t* n_dofs);
+
+/* R = R(W), the DG spatial residual of eq. dg_ns (M dW/dt + R(W) = 0, Sec. 3.1):
+ * volume term, Roe inviscid flux, BR2 viscous flux (eq. visc_flux) with the
+ * lifting of eq. re, and the dual-consistency face term.  Optional S (may be
+ * NULL): a modal source, R <- R - S.  W, S, R: device, E*m*n_m FP64; R must
+ * not alias W.  Sets DG_ERR_NONPHYSICAL in the status word if rho or p <= 0 at
+ * a quadrature point. */
+dg_status dg_residual(dg_mesh mesh, const double* W, const double* S, double* R, void* stream);
+
+#define DG_JVP_EXACT 0      /* forward-mode derivative of the discrete residual */
+#define DG_JVP_FD 1         /* eq. DG-mf with h = eps sqrt(1 + ||v||)/||W|| as printed */
+#define DG_JVP_FD_SCALED 2  /* eq. DG-mf with h = eps sqrt(1 + ||W||)/||v|| */
+
+/* Kv = sigma M v + dR/dW(W) v: the product of the iteration matrix
+ * K = M/(a_ii dt) + dR/dW of eq. ODEDG with a vector (Sec. 5.1), sigma being
+ * the shift (1/(a_ii dt) for ESDIRK, 3/(2 dt) for BDF2) and M = |J| I.
+ * DG_JVP_EXACT: exact linearisation (default).  DG_JVP_FD / _SCALED: the
+ * matrix-free finite difference of eq. DG-mf with eps = 1e-7; R_W = R(W) must
+ * then be given (device), else it may be NULL.  W, v, Kv: device FP64; Kv must
+ * not alias W or v. */
+dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma,
+                 const double* v, double* Kv, int mode, void* stream);
+
+#define DG_CYCLE_FMG 0      /* MG_full (Algorithm 1) */
+#define DG_CYCLE_V 1        /* one MG_V cycle (Algorithm 2) from a zero guess */
+#define DG_CYCLE_BJ 2       /* element block Jacobi only (no multigrid) */
+#define DG_PREC_FP64 0
+#define DG_PREC_MIXED 1     /* FP32 smoothers, blocks and fine JVP inside the preconditioner */
+
+/* p-multigrid options (Sec. 6; Table MGSettings).  p_level[0] must equal the
+ * mesh degree and the levels must decrease strictly.  Every smoother is GMRES
+ * right-preconditioned by element block Jacobi; nu_pre/nu_post per level
+ * (ignored on the coarsest), nu_coarse on the coarsest level. */
+typedef struct {
+  int n_levels;
+  int p_level[8];
+  int nu_pre[8], nu_post[8], nu_coarse;
+  int cycle;
+  int precision;
+  int fgmres_restart;   /* size of the outer FGMRES workspace allocated here (0 => 30, <= 64) */
+} dg_pmg_opts;
+
+/* Assemble the preconditioner at state W and shift sigma (once per time step:
+ * lagged, Sec. 7.4): diagonal Jacobian blocks dR_e/dW_e + sigma |J| I at the fine
+ * order, neighbour blocks at the first coarse order only (Sec. 6.3),
+ * coarse-level blocks by subspace inheritance (Sec. 6.1: with the orthonormal
+ * hierarchical basis the projection keeps the leading modes of each variable
+ * pair), and the inverse of every diagonal block by Gauss-Jordan elimination
+ * with partial pivoting (the element block Jacobi of Sec. 6.3).  W: device FP64.
+ * Allocates the handle's workspace; DG_ERR_OOM if it does not fit.  Blocks
+ * until setup is complete; a singular block gives DG_ERR_BREAKDOWN. */
+dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, const dg_pmg_opts* opts,
+                       void* stream, dg_pmg* out);
+
+/* z = P^{-1} r: one application of the preconditioner (MG_full of Algorithm 1,
+ * one MG_V of Algorithm 2, or block Jacobi), r and z device FP64, may not alias. */
+dg_status dg_pmg_apply(dg_pmg pmg, const double* r, double* z, void* stream);
+dg_status dg_pmg_destroy(dg_pmg pmg);
+
+/* FGMRES options: restart length (<= the pmg handle's fgmres_restart), restarts allowed after the first
+ * cycle, relative tolerance on the unpreconditioned residual ||b - K dW|| /
+ * ||b|| (right preconditioning, Sec. 7.4), absolute tolerance, JVP mode. */
+typedef struct {
+  int restart;
+  int max_restarts;
+  double rtol;
+  double atol;
+  int jvp_mode;
+} dg_krylov_opts;
+
+typedef struct {
+  int iters;            /* FGMRES iterations (preconditioner applications) */
+  double res0;          /* ||b|| */
+  double res_final;     /* residual estimate at exit */
+  double rho;           /* (res_final/res0)^(1/iters), Sec. 7.3 */
+  int status;           /* dg_status of the solve */
+  float ms_total;       /* device time of the call */
+} dg_krylov_stats;
+
+/* Solve K dW = b (eq. ODEDG: the caller passes b = -f of the Newton step,
+ * eq. NEWTON) by flexible GMRES (Saad 1993; Sec. 6) from dW = 0, right
+ * preconditioned by pmg (setup at the same mesh; its sigma must be the one
+ * given here), Arnoldi by classical Gram-Schmidt applied twice, Givens
+ * rotations.  The outer Krylov vectors and the JVP are FP64.  W, b, dW: device
+ * FP64.  Blocks until the solve ends (it reads the residual estimate once per
+ * iteration); stats (host, may be NULL) is filled in.  Returns DG_OK,
+ * DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN or an error of the calls above. */
+dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, const double* b,
+                         double sigma, const dg_krylov_opts* opts, double* dW,
+                         dg_krylov_stats* stats, void* stream);
+
+/* Newton right-hand side of one BDF2 step (the form of eq. NEWTON with the
+ * BDF2 shift 3/(2 dt) in place of 1/(a_ii dt)):
+ *   b = -[ M (3 Wk - 4 Wn + Wnm1) / (2 dt) + R(Wk) ],  M = |J| I.
+ * Wk (current Newton iterate), Wn, Wnm1 (previous steps), b: device FP64;
+ * b must not alias the inputs.  dt > 0. */
+dg_status dg_bdf2_rhs(dg_mesh mesh, const double* Wk, const double* Wn, const double* Wnm1, double dt,
+                      double* b, void* stream);
+
+/* y <- y + alpha x over the E*m*n_m DOFs (the Newton update W <- W + dW of
+ * eq. NEWTON).  x, y: device FP64, may not alias. */
+dg_status dg_axpy(dg_mesh mesh, double alpha, const double* x, double* y, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (host-side counter; for launch accounting in benchmarks). */
+dg_status dg_launch_count(unsigned long long* count);
+
+/* Synchronise `stream`, return the mesh's device status word (DG_OK if no
+ * device-side problem was recorded since the last call) and clear it. */
+dg_status dg_status_sync(dg_mesh mesh, void* stream);
+
+/* Sizes of the pMG workspace in bytes (blocks, vectors), for memory budgeting. */
+dg_status dg_pmg_bytes(dg_pmg pmg, size_t* block_bytes, size_t* vector_bytes);
+
+#define DG_BLOCKS_DIAG_INV 0   /* inverse diagonal blocks, E * nb * nb */
+#define DG_BLOCKS_NEIGHBOUR 1  /* neighbour blocks, E * 2d * nb * nb, [e][2k+side] */
+
+/* Copy the blocks of level `level` into a caller device buffer (entries of the
+ * handle's precision: FP64, or FP32 in mixed mode; nb = m * n_m(p_level[level]);
+ * row-major [v*n_m + i][w*n_m + j]), for testing and inspection.  Neighbour
+ * blocks exist for levels >= 1 (side 0 = the xi_k = -1 face).  Synchronous.
+ * DG_ERR_INVALID if the level or kind does not exist or out_bytes is short. */
+dg_status dg_pmg_export_blocks(dg_pmg pmg, int level, int which, void* out, size_t out_bytes,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -1,0 +1,259 @@
+"""ctypes binding of libdgpmg.so (the C ABI of include/dg.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are passed as integer device pointers, or as torch
+CUDA tensors (contiguous float64), whose data_ptr() is taken.  The library is
+loaded on first use and a missing library raises: there is no CPU path.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdgpmg.so")
+
+DG_OK = 0
+STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID", 2: "DG_ERR_OOM", 3: "DG_ERR_CUDA",
+                4: "DG_ERR_NONPHYSICAL", 5: "DG_ERR_NOT_CONVERGED", 6: "DG_ERR_BREAKDOWN",
+                7: "DG_ERR_TIMEOUT", 8: "DG_ERR_UNSUPPORTED"}
+JVP_EXACT, JVP_FD, JVP_FD_SCALED = 0, 1, 2
+CYCLE_FMG, CYCLE_V, CYCLE_BJ = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR = 0, 1
+
+EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
+            "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
+            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count"]
+
+
+class DGError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__("%s returned %s" % (fn, STATUS_NAMES.get(code, code)))
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
+                ("hi", ctypes.c_double * 3), ("p", ctypes.c_int), ("nq1d", ctypes.c_int)]
+
+
+class PhysicsDesc(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("mu", ctypes.c_double),
+                ("Rgas", ctypes.c_double), ("eta_br2", ctypes.c_double), ("roe_delta", ctypes.c_double)]
+
+
+class PmgOpts(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("p_level", ctypes.c_int * 8), ("nu_pre", ctypes.c_int * 8),
+                ("nu_post", ctypes.c_int * 8), ("nu_coarse", ctypes.c_int), ("cycle", ctypes.c_int),
+                ("precision", ctypes.c_int), ("fgmres_restart", ctypes.c_int)]
+
+
+class KrylovOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("atol", ctypes.c_double), ("jvp_mode", ctypes.c_int)]
+
+
+class KrylovStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
+                ("rho", ctypes.c_double), ("status", ctypes.c_int), ("ms_total", ctypes.c_float)]
+
+
+_lib = None
+P = ctypes.c_void_p
+
+
+def load(path=None):
+    """Load the shared library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libdgpmg.so not found at %s: build it with "
+                           "paper_1812_04789_gb300.build.build() (there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    sig = {
+        "dg_mesh_create": [ctypes.POINTER(MeshDesc), ctypes.POINTER(PhysicsDesc), P, ctypes.POINTER(P)],
+        "dg_mesh_destroy": [P],
+        "dg_mesh_info": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)],
+        "dg_residual": [P, P, P, P, P],
+        "dg_jvp": [P, P, P, ctypes.c_double, P, P, ctypes.c_int, P],
+        "dg_pmg_setup": [P, P, ctypes.c_double, ctypes.POINTER(PmgOpts), P, ctypes.POINTER(P)],
+        "dg_pmg_apply": [P, P, P, P],
+        "dg_pmg_destroy": [P],
+        "dg_fgmres_step": [P, P, P, P, ctypes.c_double, ctypes.POINTER(KrylovOpts), P,
+                           ctypes.POINTER(KrylovStats), P],
+        "dg_status_sync": [P, P],
+        "dg_pmg_bytes": [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+        "dg_pmg_export_blocks": [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_size_t, P],
+        "dg_bdf2_rhs": [P, P, P, P, ctypes.c_double, P, P],
+        "dg_axpy": [P, ctypes.c_double, P, P, P],
+        "dg_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Device pointer of a torch CUDA tensor (checked contiguous) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return x.data_ptr()
+    raise TypeError("expected a device pointer or a tensor, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(fn, code):
+    if code != DG_OK:
+        raise DGError(fn, code)
+
+
+class Mesh:
+    """Owns a dg_mesh handle (periodic structured mesh + basis tables)."""
+
+    def __init__(self, dim, n, lo, hi, p, nq1d=0, gamma=1.4, Pr=0.72, mu=0.0, Rgas=1.0, eta=0.0,
+                 roe_delta=0.1, stream=None):
+        lib = load()
+        d = MeshDesc()
+        d.dim = dim
+        n = list(n) + [1] * (3 - len(n))
+        lo = list(lo) + [0.0] * (3 - len(lo))
+        hi = list(hi) + [1.0] * (3 - len(hi))
+        for k in range(3):
+            d.n[k], d.lo[k], d.hi[k] = int(n[k]), float(lo[k]), float(hi[k])
+        d.p, d.nq1d = int(p), int(nq1d)
+        ph = PhysicsDesc(gamma, Pr, mu, Rgas, eta, roe_delta)
+        h = P()
+        _check("dg_mesh_create", lib.dg_mesh_create(ctypes.byref(d), ctypes.byref(ph), _stream(stream),
+                                                    ctypes.byref(h)))
+        self.h = h
+        self.dim, self.p = dim, p
+        E, nm, m, N = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check("dg_mesh_info", lib.dg_mesh_info(h, ctypes.byref(E), ctypes.byref(nm), ctypes.byref(m),
+                                                ctypes.byref(N)))
+        self.E, self.nm, self.m, self.ndofs = E.value, nm.value, m.value, N.value
+
+    @classmethod
+    def from_workload(cls, desc, phys, stream=None):
+        """From workloads.mesh_desc(...) / workloads.physics(...) dicts."""
+        return cls(desc["dim"], desc["n"], desc["lo"], desc["hi"], desc["p"], desc.get("nq1d", 0),
+                   gamma=phys["gamma"], Pr=phys["Pr"], mu=phys["mu"], Rgas=phys["Rgas"],
+                   eta=phys.get("eta", 0.0) or 0.0, roe_delta=phys["roe_delta"], stream=stream)
+
+    @property
+    def shape(self):
+        return (self.E, self.m, self.nm)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dg_mesh_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def residual(self, W, R, S=None, stream=None):
+        _check("dg_residual", load().dg_residual(self.h, _ptr(W), _ptr(S), _ptr(R), _stream(stream)))
+
+    def jvp(self, W, v, Kv, sigma, mode=JVP_EXACT, R_W=None, stream=None):
+        _check("dg_jvp", load().dg_jvp(self.h, _ptr(W), _ptr(R_W), float(sigma), _ptr(v), _ptr(Kv),
+                                       int(mode), _stream(stream)))
+
+    def bdf2_rhs(self, Wk, Wn, Wnm1, dt, b, stream=None):
+        """b = -[M (3 Wk - 4 Wn + Wnm1)/(2 dt) + R(Wk)] (BDF2 Newton right-hand side)."""
+        _check("dg_bdf2_rhs", load().dg_bdf2_rhs(self.h, _ptr(Wk), _ptr(Wn), _ptr(Wnm1), float(dt), _ptr(b),
+                                                 _stream(stream)))
+
+    def axpy(self, alpha, x, y, stream=None):
+        _check("dg_axpy", load().dg_axpy(self.h, float(alpha), _ptr(x), _ptr(y), _stream(stream)))
+
+    def status_sync(self, stream=None):
+        return load().dg_status_sync(self.h, _stream(stream))
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    c = ctypes.c_ulonglong()
+    _check("dg_launch_count", load().dg_launch_count(ctypes.byref(c)))
+    return c.value
+
+
+def pmg_opts(p_levels, nu_pre=10, nu_post=10, nu_coarse=30, cycle=CYCLE_FMG, precision=PREC_FP64,
+             fgmres_restart=30):
+    o = PmgOpts()
+    o.n_levels = len(p_levels)
+    for l, p in enumerate(p_levels):
+        o.p_level[l] = int(p)
+        o.nu_pre[l] = int(nu_pre[l] if hasattr(nu_pre, "__len__") else nu_pre)
+        o.nu_post[l] = int(nu_post[l] if hasattr(nu_post, "__len__") else nu_post)
+    o.nu_coarse = int(nu_coarse)
+    o.cycle = int(cycle)
+    o.precision = int(precision)
+    o.fgmres_restart = int(fgmres_restart)
+    return o
+
+
+class PMG:
+    """Owns a dg_pmg handle: blocks, inverses and workspace set up at (W, sigma)."""
+
+    def __init__(self, mesh, W, sigma, opts, stream=None):
+        h = P()
+        _check("dg_pmg_setup", load().dg_pmg_setup(mesh.h, _ptr(W), float(sigma), ctypes.byref(opts),
+                                                   _stream(stream), ctypes.byref(h)))
+        self.h = h
+        self.mesh = mesh
+        self.sigma = sigma
+        self.opts = opts
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().dg_pmg_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def apply(self, r, z, stream=None):
+        _check("dg_pmg_apply", load().dg_pmg_apply(self.h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def bytes(self):
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check("dg_pmg_bytes", load().dg_pmg_bytes(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def export_blocks(self, level, which, out, stream=None):
+        nbytes = out.numel() * out.element_size()
+        _check("dg_pmg_export_blocks", load().dg_pmg_export_blocks(self.h, int(level), int(which), _ptr(out),
+                                                                   nbytes, _stream(stream)))
+
+    def fgmres(self, W, b, dW, sigma=None, restart=30, max_restarts=0, rtol=1e-5, atol=0.0,
+               jvp_mode=JVP_EXACT, stream=None, raise_on_error=True):
+        """Solve K dW = b; returns the KrylovStats as a dict."""
+        ko = KrylovOpts(int(restart), int(max_restarts), float(rtol), float(atol), int(jvp_mode))
+        st = KrylovStats()
+        code = load().dg_fgmres_step(self.mesh.h, self.h, _ptr(W), _ptr(b),
+                                     float(self.sigma if sigma is None else sigma), ctypes.byref(ko),
+                                     _ptr(dW), ctypes.byref(st), _stream(stream))
+        out = dict(iters=st.iters, res0=st.res0, res_final=st.res_final, rho=st.rho, status=code,
+                   ms_total=st.ms_total)
+        if raise_on_error and code != DG_OK:
+            raise DGError("dg_fgmres_step", code)
+        return out

@@ -1,0 +1,534 @@
+// C ABI: residual, JVP, p-multigrid setup/apply and the FGMRES implicit-step
+// solve (Sec. 5.1, Sec. 6 with Algorithms 1-2, Sec. 6.1, Sec. 6.3, Sec. 7.4).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "dg_internal.h"
+
+using namespace dgk;
+
+#define CK(...)                                                                    \
+  do {                                                                             \
+    cudaError_t e__ = (__VA_ARGS__);                                               \
+    if (e__ != cudaSuccess) return e__ == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA; \
+  } while (0)
+#define CKE(...)                        \
+  do {                                 \
+    cudaError_t e__ = (__VA_ARGS__);   \
+    if (e__ != cudaSuccess) return e__; \
+  } while (0)
+
+namespace dgk {
+
+// ---------------------------------------------------------------- FD JVP helpers
+__global__ void sumsq_partials_kernel(const double* __restrict__ a, long N, int G, double* part) {
+  __shared__ double red[256];
+  long chunk = (N + G - 1) / G, beg = blockIdx.x * chunk, end = min(N, beg + chunk);
+  double s = 0.0;
+  for (long n = beg + threadIdx.x; n < end; n += blockDim.x) s += a[n] * a[n];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// scal[0] = ||v||, scal[1] = ||W||, scal[2] = h of eq. DG-mf
+__global__ void fd_step_kernel(const double* part, int G, double* scal, int variant, double eps) {
+  if (threadIdx.x != 0) return;
+  double sv = 0.0, sw = 0.0;
+  for (int c = 0; c < G; ++c) sv += part[c];
+  for (int c = 0; c < G; ++c) sw += part[1024 + c];
+  double nv = sqrt(sv), nw = sqrt(sw);
+  scal[0] = nv;
+  scal[1] = nw;
+  double h;
+  if (variant == 0) h = (nw > 0.0) ? eps * sqrt(1.0 + nv) / nw : eps;
+  else h = (nv > 0.0) ? eps * sqrt(1.0 + nw) / nv : 0.0;
+  scal[2] = h;
+}
+
+__global__ void fd_perturb_kernel(long N, const double* W, const double* v, const double* scal, double* out) {
+  double h = scal[2];
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
+    out[n] = W[n] + h * v[n];
+}
+
+__global__ void fd_combine_kernel(long N, const double* Rp, const double* RW, const double* v, double sdet,
+                                  const double* scal, double* out) {
+  double h = scal[2];
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
+    out[n] = (h > 0.0) ? sdet * v[n] + (Rp[n] - RW[n]) / h : sdet * v[n];
+}
+
+static cudaError_t fd_jvp(const Mesh& M, const double* W, const double* RW, double sigma, const double* v,
+                          double* out, int variant, cudaStream_t st) {
+  long N = (long)M.E * M.nb;
+  int G = (int)std::min<long>(1024, std::max<long>(1, (N + 4095) / 4096));
+  note_launch();
+  sumsq_partials_kernel<<<G, 256, 0, st>>>(v, N, G, M.partials);
+  note_launch();
+  sumsq_partials_kernel<<<G, 256, 0, st>>>(W, N, G, M.partials + 1024);
+  note_launch();
+  fd_step_kernel<<<1, 32, 0, st>>>(M.partials, G, M.scal, variant, 1e-7);
+  int gr = (int)std::min<long>((N + 255) / 256, 4096);
+  note_launch();
+  fd_perturb_kernel<<<gr, 256, 0, st>>>(N, W, v, M.scal, M.t64.fd_w);
+  CKE(cudaGetLastError());
+  CKE(launch_residual<double>(M, M.t64.fd_w, nullptr, nullptr, 0.0, false, M.t64.fd_r, st));
+  note_launch();
+  fd_combine_kernel<<<gr, 256, 0, st>>>(N, M.t64.fd_r, RW, v, sigma * M.detJ, M.scal, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- multigrid
+template <class T>
+cudaError_t MG<T>::op(int l, const T* x, T* y, cudaStream_t st) {
+  if (l == 0) return launch_residual<T>(*mesh, W, x, nullptr, sigma, true, y, st);
+  Level<T>& L = lv[l];
+  return launch_bsr<T>(L.Dop, L.O, mesh->nbr, mesh->d, x, y, L.nb, mesh->E, st);
+}
+
+// SMOOTH / SOLVE: nu iterations of GMRES right-preconditioned by block Jacobi,
+// from the current x (Algorithm 2), no restart.
+template <class T>
+cudaError_t MG<T>::smooth(int l, const T* b, T* x, int nu, cudaStream_t st) {
+  Level<T>& L = lv[l];
+  Krylov<T>& K = L.kr;
+  CKE(op(l, x, L.r, st));
+  CKE(launch_axpby<T>(L.N, 1.0, b, -1.0, L.r, st));           // r = b - A x
+  CKE(K.start(L.r, st));
+  for (int j = 0; j < nu; ++j) {
+    CKE(launch_block_apply<T>(L.Dinv, K.Vj(j), K.Zj(j), L.nb, mesh->E, st));
+    CKE(op(l, K.Zj(j), K.w, st));
+    CKE(K.arnoldi(j, st));
+  }
+  return K.update(nu, x, st);
+}
+
+// MG_V(l, b_l, x_l) of Algorithm 2 on lv[l].b / lv[l].x (x updated in place).
+template <class T>
+cudaError_t MG<T>::mg_v(int l, cudaStream_t st) {
+  const int Lc = (int)lv.size() - 1;
+  Level<T>& L = lv[l];
+  if (l == Lc) return smooth(l, L.b, L.x, nu_coarse, st);
+  CKE(smooth(l, L.b, L.x, L.nu_pre, st));
+  CKE(op(l, L.x, L.t, st));
+  CKE(launch_axpby<T>(L.N, 1.0, L.b, -1.0, L.t, st));         // r_l = b_l - A_l x_l
+  Level<T>& C = lv[l + 1];
+  CKE(launch_restrict<T>(L.t, L.nm, C.b, C.nm, (long)mesh->E * mesh->m, st));
+  CKE(cudaMemsetAsync(C.x, 0, sizeof(T) * C.N, st));
+  CKE(mg_v(l + 1, st));
+  CKE(launch_prolong<T>(C.x, C.nm, L.x, L.nm, (long)mesh->E * mesh->m, true, st));
+  return smooth(l, L.b, L.x, L.nu_post, st);
+}
+
+// One preconditioner application z = P^{-1} r.
+template <class T>
+cudaError_t MG<T>::apply(const T* r, T* z, cudaStream_t st) {
+  const int Lc = (int)lv.size() - 1;
+  const long nev = (long)mesh->E * mesh->m;
+  if (cycle == DG_CYCLE_BJ) return launch_block_apply<T>(lv[0].Dinv, r, z, lv[0].nb, mesh->E, st);
+  if (cycle == DG_CYCLE_V) {
+    CKE(cudaMemcpyAsync(lv[0].b, r, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st));
+    CKE(cudaMemsetAsync(lv[0].x, 0, sizeof(T) * lv[0].N, st));
+    CKE(mg_v(0, st));
+    return cudaMemcpyAsync(z, lv[0].x, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st);
+  }
+  // MG_full (Algorithm 1): b_l = I_0^l b_0 on every level, SOLVE on the
+  // coarsest, then for l = L-1..0: x~_l = I_{l+1}^l x_{l+1}, x_l = MG_V(l, b_l, x~_l)
+  CKE(cudaMemcpyAsync(lv[0].b, r, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st));
+  for (int l = 1; l <= Lc; ++l) CKE(launch_restrict<T>(r, lv[0].nm, lv[l].b, lv[l].nm, nev, st));
+  CKE(cudaMemsetAsync(lv[Lc].x, 0, sizeof(T) * lv[Lc].N, st));
+  CKE(smooth(Lc, lv[Lc].b, lv[Lc].x, nu_coarse, st));
+  for (int l = Lc - 1; l >= 0; --l) {
+    CKE(launch_prolong<T>(lv[l + 1].x, lv[l + 1].nm, lv[l].x, lv[l].nm, nev, false, st));
+    CKE(mg_v(l, st));
+  }
+  return cudaMemcpyAsync(z, lv[0].x, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st);
+}
+
+template struct MG<double>;
+template struct MG<float>;
+
+static cudaError_t dalloc(std::vector<void*>& list, void** p, size_t bytes, size_t* counter) {
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e == cudaSuccess) {
+    list.push_back(*p);
+    if (counter) *counter += bytes;
+  }
+  return e;
+}
+
+template <class T>
+static dg_status setup_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t st) {
+  const Mesh& M = h->mesh->m;
+  const dg_pmg_opts& o = h->opts;
+  mg.mesh = &M;
+  mg.sigma = (T)h->sigma;
+  mg.nu_coarse = o.nu_coarse;
+  mg.cycle = o.cycle;
+  const int nl = o.cycle == DG_CYCLE_BJ ? 1 : o.n_levels;
+  mg.lv.resize(nl);
+  const long N0 = (long)M.E * M.nb;
+  CK(dalloc(mg.allocs, (void**)&mg.W, sizeof(T) * N0, &h->vector_bytes));
+  if (std::is_same<T, double>::value)
+    CK(cudaMemcpyAsync(mg.W, W64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
+  else
+    CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
+  for (int l = 0; l < nl; ++l) {
+    Level<T>& L = mg.lv[l];
+    L.p = o.p_level[l];
+    L.nm = 1;
+    {
+      long c = 1;  // C(p + d, d)
+      for (int i = 1; i <= M.d; ++i) c = c * (L.p + i) / i;
+      L.nm = (int)c;
+    }
+    L.nb = M.m * L.nm;
+    L.N = (long)M.E * L.nb;
+    L.nu_pre = o.nu_pre[l];
+    L.nu_post = o.nu_post[l];
+    size_t nbl = (size_t)M.E * L.nb * L.nb;
+    CK(dalloc(mg.allocs, (void**)&L.Dinv, sizeof(T) * nbl, &h->block_bytes));
+    if (l >= 1) {
+      CK(dalloc(mg.allocs, (void**)&L.Dop, sizeof(T) * nbl, &h->block_bytes));
+      CK(dalloc(mg.allocs, (void**)&L.O, sizeof(T) * nbl * 2 * M.d, &h->block_bytes));
+    }
+    for (T** v : {&L.x, &L.b, &L.r, &L.t}) CK(dalloc(mg.allocs, (void**)v, sizeof(T) * L.N, &h->vector_bytes));
+    int nmax = (l == nl - 1) ? std::max(1, o.nu_coarse) : std::max(std::max(L.nu_pre, L.nu_post), 1);
+    if (o.cycle != DG_CYCLE_BJ) {
+      CK(L.kr.alloc(L.N, nmax));
+      h->vector_bytes += L.kr.bytes();
+    }
+  }
+  // blocks: fine diagonal (+ neighbour blocks at the first coarse order)
+  bool fits = true;
+  size_t tot = probe_scratch_elems<T>(M, nl > 1 ? mg.lv[1].nm : 0, &fits);
+  T* scratch = nullptr;
+  size_t scratch_elems = 0;
+  if (!fits) {
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    scratch_elems = tot * (size_t)std::min(M.E, 2 * nsm);
+    CK(dalloc(mg.allocs, (void**)&scratch, sizeof(T) * scratch_elems, nullptr));
+  }
+  CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, nl > 1 ? mg.lv[1].O : nullptr,
+                            nl > 1 ? mg.lv[1].nm : 0, scratch, scratch_elems, st));
+  for (int l = 1; l < nl; ++l) {
+    Level<T>& L = mg.lv[l];
+    CK(launch_truncate_blocks<T>(mg.lv[0].Dinv, mg.lv[0].nm, L.Dop, L.nm, M.m, M.E, st));
+    if (l >= 2)
+      CK(launch_truncate_blocks<T>(mg.lv[1].O, mg.lv[1].nm, L.O, L.nm, M.m, (long)M.E * 2 * M.d, st));
+    CK(cudaMemcpyAsync(L.Dinv, L.Dop, sizeof(T) * (size_t)M.E * L.nb * L.nb, cudaMemcpyDeviceToDevice, st));
+  }
+  for (int l = 0; l < nl; ++l) CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, M.E, M.status, st));
+  CK(cudaStreamSynchronize(st));
+  if (scratch) {
+    cudaFree(scratch);
+    mg.allocs.erase(std::find(mg.allocs.begin(), mg.allocs.end(), (void*)scratch));
+  }
+  return DG_OK;
+}
+
+static void free_list(std::vector<void*>& l) {
+  for (void* p : l) cudaFree(p);
+  l.clear();
+}
+
+template <class T>
+static void free_mg(MG<T>& mg) {
+  for (auto& L : mg.lv) L.kr.release();
+  free_list(mg.allocs);
+  mg.lv.clear();
+}
+
+}  // namespace dgk
+
+// ====================================================================== ABI
+extern "C" dg_status dg_residual(dg_mesh mesh, const double* W, const double* S, double* R, void* stream) {
+  if (!mesh || !W || !R || R == W || (S && S == R)) return DG_ERR_INVALID;
+  CK(launch_residual<double>(mesh->m, W, nullptr, S, 0.0, false, R, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma, const double* v,
+                            double* Kv, int mode, void* stream) {
+  if (!mesh || !W || !v || !Kv || Kv == W || Kv == v) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == DG_JVP_EXACT) {
+    CK(launch_residual<double>(mesh->m, W, v, nullptr, sigma, true, Kv, st));
+    return DG_OK;
+  }
+  if (mode != DG_JVP_FD && mode != DG_JVP_FD_SCALED) return DG_ERR_INVALID;
+  if (!R_W || R_W == Kv) return DG_ERR_INVALID;
+  CK(fd_jvp(mesh->m, W, R_W, sigma, v, Kv, mode == DG_JVP_FD ? 0 : 1, st));
+  return DG_OK;
+}
+
+static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
+  if (o->cycle != DG_CYCLE_FMG && o->cycle != DG_CYCLE_V && o->cycle != DG_CYCLE_BJ) return DG_ERR_INVALID;
+  if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
+  if (o->fgmres_restart < 0 || o->fgmres_restart > 64) return DG_ERR_INVALID;
+  if (o->cycle == DG_CYCLE_BJ) return o->p_level[0] == mesh->m.p || o->n_levels == 0 ? DG_OK : DG_ERR_INVALID;
+  if (o->n_levels < 1 || o->n_levels > 8) return DG_ERR_INVALID;
+  if (o->p_level[0] != mesh->m.p) return DG_ERR_INVALID;
+  for (int l = 1; l < o->n_levels; ++l)
+    if (o->p_level[l] < 0 || o->p_level[l] >= o->p_level[l - 1]) return DG_ERR_INVALID;
+  if (o->nu_coarse < 1 || o->nu_coarse > 256) return DG_ERR_INVALID;
+  for (int l = 0; l + 1 < o->n_levels; ++l)
+    if (o->nu_pre[l] < 0 || o->nu_post[l] < 0 || o->nu_pre[l] > 256 || o->nu_post[l] > 256) return DG_ERR_INVALID;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_pmg_destroy(dg_pmg h) {
+  if (!h) return DG_ERR_INVALID;
+  free_mg(h->mg64);
+  free_mg(h->mg32);
+  h->outer.release();
+  free_list(h->allocs);
+  delete h;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, const dg_pmg_opts* opts,
+                                  void* stream, dg_pmg* out) {
+  if (!out) return DG_ERR_INVALID;
+  *out = nullptr;
+  if (!mesh || !W || !opts || !(sigma >= 0.0)) return DG_ERR_INVALID;
+  dg_status s = check_opts(mesh, opts);
+  if (s != DG_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  dg_pmg h = new dg_pmg_s();
+  h->mesh = mesh;
+  h->opts = *opts;
+  if (h->opts.cycle == DG_CYCLE_BJ) {
+    h->opts.n_levels = 1;
+    h->opts.p_level[0] = mesh->m.p;
+  }
+  h->sigma = sigma;
+  h->precision = opts->precision;
+  CK(cudaMemsetAsync(mesh->m.status, 0, sizeof(int), st));
+  if (h->precision == DG_PREC_FP64) s = setup_mg<double>(h, h->mg64, W, st);
+  else s = setup_mg<float>(h, h->mg32, W, st);
+  const long N0 = (long)mesh->m.E * mesh->m.nb;
+  if (s == DG_OK && h->precision == DG_PREC_MIXED) {
+    if (dalloc(h->allocs, (void**)&h->r32, sizeof(float) * N0, &h->vector_bytes) != cudaSuccess ||
+        dalloc(h->allocs, (void**)&h->z32, sizeof(float) * N0, &h->vector_bytes) != cudaSuccess)
+      s = DG_ERR_OOM;
+  }
+  if (s == DG_OK) {
+    h->outer_restart = opts->fgmres_restart > 0 ? opts->fgmres_restart : 30;
+    if (h->outer.alloc(N0, h->outer_restart) != cudaSuccess ||
+        dalloc(h->allocs, (void**)&h->tmp64, sizeof(double) * N0 * 2, &h->vector_bytes) != cudaSuccess)
+      s = DG_ERR_OOM;
+    else
+      h->vector_bytes += h->outer.bytes();
+  }
+  if (s == DG_OK) {
+    int hs = 0;
+    if (cudaMemcpyAsync(&hs, mesh->m.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      s = DG_ERR_CUDA;
+    else if (hs & ST_SINGULAR)
+      s = DG_ERR_BREAKDOWN;
+    else if (hs & ST_NONPHYSICAL)
+      s = DG_ERR_NONPHYSICAL;
+  }
+  if (s != DG_OK) {
+    dg_pmg_destroy(h);
+    return s;
+  }
+  *out = h;
+  return DG_OK;
+}
+
+static dg_status pmg_apply_impl(dg_pmg h, const double* r, double* z, cudaStream_t st) {
+  const long N0 = (long)h->mesh->m.E * h->mesh->m.nb;
+  if (h->precision == DG_PREC_FP64) {
+    CK(h->mg64.apply(r, z, st));
+  } else {
+    CK(launch_convert<double, float>(N0, r, h->r32, st));
+    CK(h->mg32.apply(h->r32, h->z32, st));
+    CK(launch_convert<float, double>(N0, h->z32, z, st));
+  }
+  return DG_OK;
+}
+
+extern "C" dg_status dg_pmg_apply(dg_pmg h, const double* r, double* z, void* stream) {
+  if (!h || !r || !z || r == z) return DG_ERR_INVALID;
+  return pmg_apply_impl(h, r, z, (cudaStream_t)stream);
+}
+
+extern "C" dg_status dg_pmg_bytes(dg_pmg h, size_t* block_bytes, size_t* vector_bytes) {
+  if (!h) return DG_ERR_INVALID;
+  if (block_bytes) *block_bytes = h->block_bytes;
+  if (vector_bytes) *vector_bytes = h->vector_bytes;
+  return DG_OK;
+}
+
+extern "C" dg_status dg_pmg_export_blocks(dg_pmg h, int level, int which, void* out, size_t out_bytes,
+                                          void* stream) {
+  if (!h || !out) return DG_ERR_INVALID;
+  const Mesh& M = h->mesh->m;
+  int nl = (int)(h->precision == DG_PREC_FP64 ? h->mg64.lv.size() : h->mg32.lv.size());
+  if (level < 0 || level >= nl) return DG_ERR_INVALID;
+  size_t es = h->precision == DG_PREC_FP64 ? sizeof(double) : sizeof(float);
+  int nb = h->precision == DG_PREC_FP64 ? h->mg64.lv[level].nb : h->mg32.lv[level].nb;
+  const void* src;
+  size_t cnt;
+  if (which == DG_BLOCKS_DIAG_INV) {
+    src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].Dinv : (const void*)h->mg32.lv[level].Dinv;
+    cnt = (size_t)M.E * nb * nb;
+  } else if (which == DG_BLOCKS_NEIGHBOUR) {
+    if (level < 1) return DG_ERR_INVALID;
+    src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].O : (const void*)h->mg32.lv[level].O;
+    cnt = (size_t)M.E * 2 * M.d * nb * nb;
+  } else {
+    return DG_ERR_INVALID;
+  }
+  if (out_bytes < cnt * es) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(out, src, cnt * es, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, const double* b, double sigma,
+                                    const dg_krylov_opts* kopts, double* dW, dg_krylov_stats* stats,
+                                    void* stream) {
+  if (!mesh || !pmg || !W || !b || !kopts || !dW || dW == b || dW == W) return DG_ERR_INVALID;
+  if (pmg->mesh != mesh) return DG_ERR_INVALID;
+  const int restart = kopts->restart > 0 ? kopts->restart : 30;
+  if (restart > pmg->outer_restart || kopts->max_restarts < 0 || !(kopts->rtol >= 0.0) || !(kopts->atol >= 0.0))
+    return DG_ERR_INVALID;
+  const int mode = kopts->jvp_mode;
+  if (mode != DG_JVP_EXACT && mode != DG_JVP_FD && mode != DG_JVP_FD_SCALED) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Mesh& M = mesh->m;
+  const long N = (long)M.E * M.nb;
+  Krylov<double>& K = pmg->outer;
+  double* RW = pmg->tmp64;            // R(W) for the FD mode
+  double* rr = pmg->tmp64 + N;        // restart residual
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  auto kv = [&](const double* x, double* y) -> dg_status {
+    if (mode == DG_JVP_EXACT) {
+      CK(launch_residual<double>(M, W, x, nullptr, sigma, true, y, st));
+    } else {
+      CK(fd_jvp(M, W, RW, sigma, x, y, mode == DG_JVP_FD ? 0 : 1, st));
+    }
+    return DG_OK;
+  };
+  dg_status s = DG_OK;
+  int iters = 0;
+  double bnorm = 0, res = 0, host[3];
+  bool converged = false;
+  if (mode != DG_JVP_EXACT) {
+    if (launch_residual<double>(M, W, nullptr, nullptr, 0.0, false, RW, st) != cudaSuccess) s = DG_ERR_CUDA;
+  }
+  if (s == DG_OK && cudaMemsetAsync(dW, 0, sizeof(double) * N, st) != cudaSuccess) s = DG_ERR_CUDA;
+  for (int cycle = 0; s == DG_OK && cycle <= kopts->max_restarts && !converged; ++cycle) {
+    const double* r0 = b;
+    if (cycle > 0) {
+      if ((s = kv(dW, rr)) != DG_OK) break;
+      if (launch_axpby<double>(N, 1.0, b, -1.0, rr, st) != cudaSuccess) { s = DG_ERR_CUDA; break; }
+      r0 = rr;
+    }
+    if (K.start(r0, st) != cudaSuccess) { s = DG_ERR_CUDA; break; }
+    if (cudaMemcpyAsync(host, K.res + 1, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) { s = DG_ERR_CUDA; break; }
+    double beta = host[0];
+    if (cycle == 0) bnorm = beta;
+    const double tol = std::max(kopts->rtol * bnorm, kopts->atol);
+    res = beta;
+    if (!(beta > tol)) { converged = true; break; }
+    int jdone = 0;
+    for (int j = 0; j < restart; ++j) {
+      if ((s = pmg_apply_impl(pmg, K.Vj(j), K.Zj(j), st)) != DG_OK) break;
+      if ((s = kv(K.Zj(j), K.w)) != DG_OK) break;
+      if (K.arnoldi(j, st) != cudaSuccess) { s = DG_ERR_CUDA; break; }
+      ++iters;
+      jdone = j + 1;
+      int kd[2];
+      if (cudaMemcpyAsync(host, K.res, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(kd, K.kdim, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess) { s = DG_ERR_CUDA; break; }
+      res = host[0];
+      if (kd[1] & ST_NONFINITE || !isfinite(res)) { s = DG_ERR_BREAKDOWN; break; }
+      if (res <= tol) { converged = true; break; }
+      if (kd[0] <= j) { converged = res <= tol; break; }   // happy breakdown
+    }
+    if (s != DG_OK) break;
+    if (K.update(jdone, dW, st) != cudaSuccess) { s = DG_ERR_CUDA; break; }
+  }
+  cudaEventRecord(e1, st);
+  float ms = 0.f;
+  if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == DG_OK && !converged) s = DG_ERR_NOT_CONVERGED;
+  if (s == DG_OK) {
+    int hs = 0;
+    cudaMemcpy(&hs, M.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (hs & ST_NONPHYSICAL) s = DG_ERR_NONPHYSICAL;
+  }
+  if (stats) {
+    stats->iters = iters;
+    stats->res0 = bnorm;
+    stats->res_final = res;
+    stats->rho = (iters > 0 && bnorm > 0) ? pow(res / bnorm, 1.0 / iters) : 0.0;
+    stats->status = s;
+    stats->ms_total = ms;
+  }
+  return s;
+}
+
+namespace dgk {
+unsigned long long& launch_counter() {
+  static unsigned long long n = 0;
+  return n;
+}
+
+__global__ void bdf2_rhs_kernel(long N, const double* __restrict__ Wk, const double* __restrict__ Wn,
+                                const double* __restrict__ Wnm1, double c, double* __restrict__ b) {
+  // on entry b holds R(Wk)
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
+    b[n] = -(c * (3.0 * Wk[n] - 4.0 * Wn[n] + Wnm1[n]) + b[n]);
+}
+}  // namespace dgk
+
+extern "C" dg_status dg_bdf2_rhs(dg_mesh mesh, const double* Wk, const double* Wn, const double* Wnm1, double dt,
+                                 double* b, void* stream) {
+  if (!mesh || !Wk || !Wn || !Wnm1 || !b || b == Wk || b == Wn || b == Wnm1 || !(dt > 0.0)) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Mesh& M = mesh->m;
+  const long N = (long)M.E * M.nb;
+  CK(launch_residual<double>(M, Wk, nullptr, nullptr, 0.0, false, b, st));
+  int gr = (int)std::min<long>((N + 255) / 256, 4096);
+  note_launch();
+  bdf2_rhs_kernel<<<gr, 256, 0, st>>>(N, Wk, Wn, Wnm1, M.detJ / (2.0 * dt), b);
+  CK(cudaGetLastError());
+  return DG_OK;
+}
+
+extern "C" dg_status dg_axpy(dg_mesh mesh, double alpha, const double* x, double* y, void* stream) {
+  if (!mesh || !x || !y || x == y) return DG_ERR_INVALID;
+  const long N = (long)mesh->m.E * mesh->m.nb;
+  CK(launch_axpby<double>(N, alpha, x, 1.0, y, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+extern "C" dg_status dg_launch_count(unsigned long long* count) {
+  if (!count) return DG_ERR_INVALID;
+  *count = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED);
+  return DG_OK;
+}

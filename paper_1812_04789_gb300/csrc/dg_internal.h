@@ -1,0 +1,171 @@
+// Internal declarations shared by the library's translation units: handle
+// structures, kernel launchers and the Krylov workspace.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_common.cuh"
+
+namespace dgk {
+
+enum : int { ST_NONPHYSICAL = 1, ST_SINGULAR = 2, ST_NONFINITE = 4 };
+
+// host-side count of kernel launches (dg_launch_count)
+unsigned long long& launch_counter();
+inline void note_launch() { __atomic_fetch_add(&launch_counter(), 1ULL, __ATOMIC_RELAXED); }
+
+// Device tables of one precision (see MeshView for the layouts).
+template <class T>
+struct Tables {
+  T *vphiT = nullptr, *vdphiT = nullptr, *vphi = nullptr, *vdphi = nullptr, *vw = nullptr;
+  T *fphiT = nullptr, *fdphiT = nullptr, *fphi = nullptr, *fdphi = nullptr, *fw = nullptr;
+  T* lift = nullptr;
+  T* slots = nullptr;        // face slots [E][d][2][nb]
+  T* fd_w = nullptr;         // finite-difference JVP scratch: W + h v
+  T* fd_r = nullptr;         // finite-difference JVP scratch: R(W + h v)
+};
+
+struct Mesh {
+  dg_mesh_desc desc;
+  dg_physics phys;
+  int d, m, p, nq1d, nm, nb, nq, nqf, E;
+  double h[3], detJ, faceJ[3];
+  int* nbr = nullptr;        // device [E][d][2]
+  Tables<double> t64;
+  Tables<float> t32;
+  int* status = nullptr;     // device status word
+  double* scal = nullptr;    // device scalars for the FD JVP (norms, h)
+  double* partials = nullptr;// reduction partials for the FD JVP norms
+  std::vector<void*> allocs;
+  template <class T> MeshView<T> view() const;
+  template <class T> Phys<T> phys_t() const;
+};
+
+// ----------------------------------------------------------------- kernels
+// Residual (jvp = false) or exact JVP (jvp = true) in precision T:
+// out = [R(W) - S] or [sigma |J| V + dR/dW(W) V].
+template <class T>
+cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
+                            T* out, cudaStream_t st);
+
+// Element Jacobian blocks by probing: D[e] = dR_e/dW_e + sigma |J| I (nb x nb),
+// and when O != nullptr the neighbour blocks O[e][2k+side] restricted to the
+// first nmc modes of every variable (nbc x nbc, nbc = m nmc).
+template <class T>
+cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, T* O, int nmc,
+                                T* scratch, size_t scratch_elems, cudaStream_t st);
+template <class T>
+size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem);
+
+// Batched in-place inverse of nblk blocks of size nb (Gauss-Jordan, partial pivoting).
+template <class T>
+cudaError_t launch_block_inverse(T* A, int nb, long nblk, int* status, cudaStream_t st);
+
+// Leading sub-block per variable pair: dst[b] (m nmt)^2 from src[b] (m nms)^2.
+template <class T>
+cudaError_t launch_truncate_blocks(const T* src, int nms, T* dst, int nmt, int m, long nblk,
+                                   cudaStream_t st);
+
+// z[e] = Ainv[e] r[e]
+template <class T>
+cudaError_t launch_block_apply(const T* A, const T* r, T* z, int nb, int E, cudaStream_t st);
+
+// y = D x + sum_s O_s x_nbr(s)
+template <class T>
+cudaError_t launch_bsr(const T* D, const T* O, const int* nbr, int d, const T* x, T* y, int nb,
+                       int E, cudaStream_t st);
+
+// vector helpers
+template <class T> cudaError_t launch_axpby(long n, double a, const T* x, double b, T* y, cudaStream_t st);
+template <class A, class B> cudaError_t launch_convert(long n, const A* x, B* y, cudaStream_t st);
+template <class T> cudaError_t launch_restrict(const T* xf, int nmf, T* xc, int nmc, long nev, cudaStream_t st);
+template <class T> cudaError_t launch_prolong(const T* xc, int nmc, T* xf, int nmf, long nev, bool add, cudaStream_t st);
+
+// ----------------------------------------------------------------- Krylov
+// Right-preconditioned (F)GMRES workspace on the device.  All scalars (H, g,
+// Givens, y, residual) stay in device memory; nothing is read back unless
+// the host asks for the residual estimate.
+template <class T>
+struct Krylov {
+  long N = 0;
+  int nmax = 0;
+  int G = 0;                 // reduction CTAs (fixed => deterministic sums)
+  T* V = nullptr;            // (nmax+1) x N
+  T* Z = nullptr;            // nmax x N
+  T* w = nullptr;            // N
+  double* H = nullptr;       // (nmax+1) x nmax, column-major
+  double* cs = nullptr;
+  double* sn = nullptr;
+  double* g = nullptr;       // nmax+1
+  double* y = nullptr;       // nmax
+  double* part = nullptr;    // (nmax+1) x G reduction partials
+  double* res = nullptr;     // residual estimate |g[j+1]|
+  int* kdim = nullptr;       // [0] effective Krylov dimension (breakdown), [1] status bits
+  std::vector<void*> allocs;
+  cudaError_t alloc(long N, int nmax);
+  void release();
+  size_t bytes() const;
+  // v0 = r / ||r||, g = (||r||, 0, ...)
+  cudaError_t start(const T* r, cudaStream_t st);
+  // after w = A z_j (w holds it): CGS2 against V[0..j], normalise into V[j+1],
+  // Givens update of column j; writes |g[j+1]| to res
+  cudaError_t arnoldi(int j, cudaStream_t st);
+  // x += Z y with H[:k,:k] y = g[:k], k = min(kdone, kdim)
+  cudaError_t update(int kdone, T* x, cudaStream_t st);
+  T* Vj(int j) { return V + (size_t)j * N; }
+  T* Zj(int j) { return Z + (size_t)j * N; }
+};
+
+// ----------------------------------------------------------------- pMG
+template <class T>
+struct Level {
+  int p = 0, nm = 0, nb = 0;
+  long N = 0;
+  T* Dinv = nullptr;         // inverse diagonal blocks [E][nb][nb]
+  T* Dop = nullptr;          // diagonal blocks of the inherited operator (l >= 1)
+  T* O = nullptr;            // neighbour blocks [E][2d][nb][nb] (l >= 1)
+  T *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  int nu_pre = 0, nu_post = 0;
+  Krylov<T> kr;
+};
+
+template <class T>
+struct MG {
+  const Mesh* mesh = nullptr;
+  std::vector<Level<T>> lv;
+  T* W = nullptr;            // state in precision T (fine JVP operator)
+  T sigma = 0;
+  int nu_coarse = 0;
+  int cycle = 0;
+  std::vector<void*> allocs;
+  cudaError_t op(int l, const T* x, T* y, cudaStream_t st);
+  cudaError_t smooth(int l, const T* b, T* x, int nu, cudaStream_t st);
+  cudaError_t mg_v(int l, cudaStream_t st);           // on lv[l].b, lv[l].x
+  cudaError_t apply(const T* r, T* z, cudaStream_t st);
+};
+
+}  // namespace dgk
+
+struct dg_mesh_s {
+  dgk::Mesh m;
+};
+
+struct dg_pmg_s {
+  dg_mesh mesh = nullptr;
+  dg_pmg_opts opts;
+  double sigma = 0;
+  int precision = 0;
+  dgk::MG<double> mg64;
+  dgk::MG<float> mg32;
+  double* r_in = nullptr;    // staging for mixed precision
+  float* r32 = nullptr;
+  float* z32 = nullptr;
+  dgk::Krylov<double> outer; // FGMRES workspace (allocated at first solve)
+  int outer_restart = 0;
+  double* tmp64 = nullptr;
+  std::vector<void*> allocs;
+  size_t block_bytes = 0, vector_bytes = 0;
+};

@@ -1,0 +1,312 @@
+// DG residual and exact Jacobian-vector product kernels (Sec. 3.1 eq. dg_ns with
+// the Roe flux, the BR2 viscous flux of eq. visc_flux and the lifting of eq. re;
+// Sec. 5.1 eq. ODEDG).
+//
+// Two kernels per evaluation:
+//  face_kernel   one pass over the d*E faces (face (k, e) joins element e, on its
+//                xi_k = +1 side, to its +e_k neighbour).  Per face point: traces
+//                of u and grad u on both sides, Roe flux, averaged viscous flux,
+//                the BR2 lifting of the jump on both sides (a face-point operator
+//                applied through shared memory), the dual-consistency tensors.
+//                The projections onto both elements' test functions go to face
+//                slots [e][k][side][v][i] (no atomics).
+//  volume_kernel one pass over the elements: interpolation of u and grad u at the
+//                volume points, F_c + F_v, projection onto grad phi_i, then the
+//                2d face slots of the element in fixed order (deterministic sums),
+//                plus sigma |J| v for a JVP or minus a source for a residual.
+// With S = Dual<T> the same code carries the directional derivative: the JVP
+// is the exact linearisation of the discrete residual.
+#include "dg_internal.h"
+
+namespace dgk {
+
+template <class T>
+__device__ __forceinline__ int dof(int nm, int v, int i) {
+  return v * nm + i;
+}
+
+// ---------------------------------------------------------------- face kernel
+template <int D, class T, bool JVP>
+__global__ void __launch_bounds__(128) face_kernel(MeshView<T> mv, Phys<T> ph,
+                                                   const T* __restrict__ W,
+                                                   const T* __restrict__ V,
+                                                   T* __restrict__ slots, int* status, int fpc) {
+  using S = typename std::conditional<JVP, Dual<T>, T>::type;
+  constexpr int M = D + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int nb = mv.nb, nm = mv.nm, nqf = mv.nqf, E = mv.E;
+  const int nfaces = D * E;
+  const int f0 = blockIdx.x * fpc;
+  const int nloc = min(fpc, nfaces - f0);
+  if (nloc <= 0) return;
+  // shared layout
+  T* sW = sm;                                   // [fpc][2][nb]
+  T* sV = sW + (size_t)fpc * 2 * nb;            // [fpc][2][nb] (JVP)
+  T* sG = sV + (JVP ? (size_t)fpc * 2 * nb : 0);// [fpc][2][nqf][M]  normal column of K(u)(jump n)
+  T* sF = sG + (size_t)fpc * 2 * nqf * M;       // [fpc][nqf][M]     flux (Roe + avg F_v, + lifting)
+  T* sD = sF + (size_t)fpc * nqf * M;           // [fpc][2][nqf][M][D]  dual tensors / 2
+  // phase 0: stage the modal coefficients of both elements of every face
+  for (int t = threadIdx.x; t < nloc * 2 * nb; t += blockDim.x) {
+    int fl = t / (2 * nb), r = t % (2 * nb), side = r / nb, j = r % nb;
+    int f = f0 + fl, k = f / E, e = f % E;
+    int el = side == 0 ? e : mv.nbr[(e * D + k) * 2 + 1];
+    sW[t] = W[(size_t)el * nb + j];
+    if (JVP) sV[t] = V[(size_t)el * nb + j];
+  }
+  __syncthreads();
+  // phase 1: pointwise physics at the face points
+  for (int t = threadIdx.x; t < nloc * nqf; t += blockDim.x) {
+    int fl = t / nqf, q = t % nqf;
+    int f = f0 + fl, k = f / E;
+    int fL = 2 * k + 1, fR = 2 * k;           // local face of L (xi_k = +1) and R (xi_k = -1)
+    S uL[M], uR[M], gL[M][D], gR[M][D];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      uL[v] = T(0);
+      uR[v] = T(0);
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        gL[v][kk] = T(0);
+        gR[v][kk] = T(0);
+      }
+    }
+    const T* wL = sW + (size_t)fl * 2 * nb;
+    const T* wR = wL + nb;
+    const T* vL = sV + (size_t)fl * 2 * nb;
+    const T* vR = vL + nb;
+    for (int i = 0; i < nm; ++i) {
+      T pL = mv.fphiT[((size_t)fL * nm + i) * nqf + q];
+      T pR = mv.fphiT[((size_t)fR * nm + i) * nqf + q];
+      T dL[D], dR[D];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        dL[kk] = mv.fdphiT[(((size_t)fL * D + kk) * nm + i) * nqf + q];
+        dR[kk] = mv.fdphiT[(((size_t)fR * D + kk) * nm + i) * nqf + q];
+      }
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        S a, b;
+        if constexpr (JVP) {
+          a = S(wL[v * nm + i], vL[v * nm + i]);
+          b = S(wR[v * nm + i], vR[v * nm + i]);
+        } else {
+          a = wL[v * nm + i];
+          b = wR[v * nm + i];
+        }
+        uL[v] = uL[v] + a * pL;
+        uR[v] = uR[v] + b * pR;
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) {
+          gL[v][kk] = gL[v][kk] + a * dL[kk];
+          gR[v][kk] = gR[v][kk] + b * dR[kk];
+        }
+      }
+    }
+    if (!physical<D>(uL, (double)ph.gm1) || !physical<D>(uR, (double)ph.gm1))
+      atomicOr(status, ST_NONPHYSICAL);
+    S fp[M], GLn[M], GRn[M], DL[M][D], DR[M][D];
+    face_point_k<D, S, T>(k, uL, gL, uR, gR, ph, fp, GLn, GRn, DL, DR);
+    T* g0 = sG + ((size_t)fl * 2 * nqf + q) * M;
+    T* g1 = sG + ((size_t)(fl * 2 + 1) * nqf + q) * M;
+    T* fo = sF + ((size_t)fl * nqf + q) * M;
+    T* d0 = sD + (((size_t)fl * 2) * nqf + q) * M * D;
+    T* d1 = sD + (((size_t)fl * 2 + 1) * nqf + q) * M * D;
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      fo[v] = JVP ? tan_part(fp[v]) : val(fp[v]);
+      g0[v] = JVP ? tan_part(GLn[v]) : val(GLn[v]);
+      g1[v] = JVP ? tan_part(GRn[v]) : val(GRn[v]);
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) {
+        d0[v * D + kk] = JVP ? tan_part(DL[v][kk]) : val(DL[v][kk]);
+        d1[v * D + kk] = JVP ? tan_part(DR[v][kk]) : val(DR[v][kk]);
+      }
+    }
+  }
+  __syncthreads();
+  // phase 2: BR2 lifting on both sides, fhat = Roe + {F_v}.n + eta {delta}.n
+  for (int t = threadIdx.x; t < nloc * nqf; t += blockDim.x) {
+    int fl = t / nqf, q = t % nqf;
+    int k = (f0 + fl) / E;
+    const T* PL = mv.lift + ((size_t)(2 * k + 1) * nqf + q) * nqf;
+    const T* PR = mv.lift + ((size_t)(2 * k) * nqf + q) * nqf;
+    T dl[M], dr[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) dl[v] = dr[v] = T(0);
+    for (int q2 = 0; q2 < nqf; ++q2) {
+      T a = PL[q2], b = PR[q2];
+      const T* g0 = sG + ((size_t)fl * 2 * nqf + q2) * M;
+      const T* g1 = sG + ((size_t)(fl * 2 + 1) * nqf + q2) * M;
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        dl[v] += a * g0[v];
+        dr[v] += b * g1[v];
+      }
+    }
+    T* fo = sF + ((size_t)fl * nqf + q) * M;
+#pragma unroll
+    for (int v = 0; v < M; ++v) fo[v] += ph.eta * T(0.5) * (dl[v] + dr[v]);
+  }
+  __syncthreads();
+  // phase 3: projection onto the test functions of both elements
+  for (int t = threadIdx.x; t < nloc * 2 * nb; t += blockDim.x) {
+    int fl = t / (2 * nb), r = t % (2 * nb), side = r / nb, j = r % nb;
+    int v = j / nm, i = j % nm;
+    int f = f0 + fl, k = f / E, e = f % E;
+    int lf = side == 0 ? 2 * k + 1 : 2 * k;
+    T sgn = side == 0 ? T(1) : T(-1);
+    const T* fw = mv.fw + (size_t)k * nqf;
+    const T* ph_ = mv.fphi + (size_t)lf * nqf * nm;
+    const T* dph = mv.fdphi + (size_t)lf * D * nqf * nm;
+    const T* Fo = sF + (size_t)fl * nqf * M;
+    const T* Dd = sD + ((size_t)(fl * 2 + side) * nqf) * M * D;
+    T acc = T(0);
+    for (int q = 0; q < nqf; ++q) {
+      T s = sgn * ph_[(size_t)q * nm + i] * Fo[q * M + v];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) s -= dph[((size_t)kk * nqf + q) * nm + i] * Dd[(q * M + v) * D + kk];
+      acc += fw[q] * s;
+    }
+    slots[(((size_t)e * D + k) * 2 + side) * nb + j] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- volume kernel
+template <int D, class T, bool JVP>
+__global__ void __launch_bounds__(256) volume_kernel(MeshView<T> mv, Phys<T> ph,
+                                                     const T* __restrict__ W,
+                                                     const T* __restrict__ V,
+                                                     const T* __restrict__ slots,
+                                                     const T* __restrict__ Src, T sigma,
+                                                     T* __restrict__ out, int* status, int epc) {
+  using S = typename std::conditional<JVP, Dual<T>, T>::type;
+  constexpr int M = D + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int nb = mv.nb, nm = mv.nm, nq = mv.nq, E = mv.E;
+  const int e0 = blockIdx.x * epc;
+  const int nloc = min(epc, E - e0);
+  if (nloc <= 0) return;
+  T* sW = sm;                                  // [epc][nb]
+  T* sV = sW + (size_t)epc * nb;               // [epc][nb]
+  T* sF = sV + (JVP ? (size_t)epc * nb : 0);   // [epc][nq][M][D]  w_q |J| F
+  for (int t = threadIdx.x; t < nloc * nb; t += blockDim.x) {
+    sW[t] = W[(size_t)e0 * nb + t];
+    if (JVP) sV[t] = V[(size_t)e0 * nb + t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nloc * nq; t += blockDim.x) {
+    int el = t / nq, q = t % nq;
+    const T* w = sW + (size_t)el * nb;
+    const T* vv = sV + (size_t)el * nb;
+    S u[M], g[M][D];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      u[v] = T(0);
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) g[v][kk] = T(0);
+    }
+    for (int i = 0; i < nm; ++i) {
+      T p = mv.vphiT[(size_t)i * nq + q];
+      T dp[D];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) dp[kk] = mv.vdphiT[((size_t)kk * nm + i) * nq + q];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        S a;
+        if constexpr (JVP) a = S(w[v * nm + i], vv[v * nm + i]);
+        else a = w[v * nm + i];
+        u[v] = u[v] + a * p;
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) g[v][kk] = g[v][kk] + a * dp[kk];
+      }
+    }
+    if (!physical<D>(u, (double)ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
+    S F[M][D];
+    flux_total<D, S, T>(u, g, F, ph);
+    T wq = mv.vw[q];
+    T* fo = sF + ((size_t)el * nq + q) * M * D;
+#pragma unroll
+    for (int v = 0; v < M; ++v)
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) fo[v * D + kk] = wq * (JVP ? tan_part(F[v][kk]) : val(F[v][kk]));
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nloc * nb; t += blockDim.x) {
+    int el = t / nb, j = t % nb;
+    int v = j / nm, i = j % nm;
+    int e = e0 + el;
+    const T* fo = sF + (size_t)el * nq * M * D;
+    T acc = T(0);
+    for (int q = 0; q < nq; ++q) {
+      const T* fq = fo + (size_t)q * M * D + v * D;
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) acc -= mv.vdphi[((size_t)kk * nq + q) * nm + i] * fq[kk];
+    }
+    // face contributions in fixed order: for each direction, own +k face then -k face
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      int em = mv.nbr[(e * D + k) * 2 + 0];
+      acc += slots[(((size_t)e * D + k) * 2 + 0) * nb + j];
+      acc += slots[(((size_t)em * D + k) * 2 + 1) * nb + j];
+    }
+    if (JVP) acc += sigma * mv.detJ * sV[t];
+    else if (Src) acc -= Src[(size_t)e * nb + j];
+    out[(size_t)e * nb + j] = acc;
+  }
+}
+
+template <class T>
+static size_t face_smem(const Mesh& M, int fpc, bool jvp) {
+  return sizeof(T) * (size_t)fpc *
+         (2 * M.nb * (jvp ? 2 : 1) + 2 * M.nqf * M.m + M.nqf * M.m + 2 * M.nqf * M.m * M.d);
+}
+template <class T>
+static size_t vol_smem(const Mesh& M, int epc, bool jvp) {
+  return sizeof(T) * (size_t)epc * (M.nb * (jvp ? 2 : 1) + M.nq * M.m * M.d);
+}
+
+template <int D, class T, bool JVP>
+static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T* S, T sigma, T* out,
+                                cudaStream_t st) {
+  MeshView<T> mv = Ms.view<T>();
+  Phys<T> ph = Ms.phys_t<T>();
+  T* slots = std::is_same<T, double>::value ? (T*)Ms.t64.slots : (T*)Ms.t32.slots;
+  int fpc = std::max(1, 128 / Ms.nqf);
+  size_t fsm = face_smem<T>(Ms, fpc, JVP);
+  while (fsm > 200 * 1024 && fpc > 1) fsm = face_smem<T>(Ms, --fpc, JVP);
+  if (fsm > 48 * 1024)
+    cudaFuncSetAttribute(face_kernel<D, T, JVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+  int nfaces = D * Ms.E;
+  note_launch();
+  face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int epc = std::max(1, 256 / Ms.nq);
+  size_t vsm = vol_smem<T>(Ms, epc, JVP);
+  while (vsm > 200 * 1024 && epc > 1) vsm = vol_smem<T>(Ms, --epc, JVP);
+  if (vsm > 48 * 1024)
+    cudaFuncSetAttribute(volume_kernel<D, T, JVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+  note_launch();
+  volume_kernel<D, T, JVP><<<(Ms.E + epc - 1) / epc, 256, vsm, st>>>(mv, ph, W, V, slots, S, sigma, out,
+                                                                    Ms.status, epc);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
+                            T* out, cudaStream_t st) {
+  if (M.d == 2)
+    return jvp ? run_residual<2, T, true>(M, W, V, S, sigma, out, st)
+               : run_residual<2, T, false>(M, W, V, S, sigma, out, st);
+  return jvp ? run_residual<3, T, true>(M, W, V, S, sigma, out, st)
+             : run_residual<3, T, false>(M, W, V, S, sigma, out, st);
+}
+
+template cudaError_t launch_residual<double>(const Mesh&, const double*, const double*, const double*,
+                                             double, bool, double*, cudaStream_t);
+template cudaError_t launch_residual<float>(const Mesh&, const float*, const float*, const float*, float,
+                                            bool, float*, cudaStream_t);
+
+}  // namespace dgk
