@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Implicit-step benchmark: one BDF2 time step of the compressible Navier-Stokes
+equations with the matrix-free modal DG discretisation, solved by Newton with
+p-multigrid preconditioned FGMRES, on the Taylor-Green vortex workload
+(16^3 hexes, p = 4, pMG 4-2-1-0, FGMRES(30) tol 1e-5).
+
+A step = preconditioner update at W^n (lagged for the step) + `--newton`
+Newton iterations, each: BDF2 right-hand side, FGMRES solve, state update.
+Every step starts from the same (W^n, W^{n-1}) so every step does the same
+work.  Metric: implicit-step DOFs/s = DOFs x steps / time.
+
+Prints one JSON line (rank 0).  `--impl reference` times the plain CPU oracle
+(test infrastructure) on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1812_04789_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "Implicit-step DOFs/s (mixed vs FP64, 1 GB300); JVP % HBM roofline; p99 latency"
+UNIT = "DOFs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="tgv16_p4")
+    ap.add_argument("--newton", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def bench_opts(cfg):
+    nl = len(cfg["p_levels"])
+    return dict(p_levels=cfg["p_levels"], nu_pre=10, nu_post=10, nu_coarse=30,
+                cycle=0 if nl > 1 else 2)
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+class Stepper:
+    """One BDF2 implicit step on the device through the library's C ABI."""
+
+    def __init__(self, B, torch, cfg, precision, stream, W0, Wm1):
+        self.B, self.torch = B, torch
+        self.cfg = cfg
+        self.stream = stream
+        desc, phys = wl.mesh_desc(cfg), wl.physics(cfg)
+        self.mesh = B.Mesh.from_workload(desc, phys, stream=stream)
+        self.dt = wl.time_step(cfg)
+        self.sigma = 1.5 / self.dt
+        o = bench_opts(cfg)
+        self.opts = B.pmg_opts(o["p_levels"], nu_pre=o["nu_pre"], nu_post=o["nu_post"],
+                               nu_coarse=o["nu_coarse"], cycle=o["cycle"], precision=precision)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.W0 = torch.from_numpy(W0).to(dev)
+        self.Wm1 = torch.from_numpy(Wm1).to(dev)
+        self.Wn = torch.empty_like(self.W0)
+        self.Wnm1 = torch.empty_like(self.W0)
+        self.Wk = torch.empty_like(self.W0)
+        self.b = torch.empty_like(self.W0)
+        self.dW = torch.empty_like(self.W0)
+        self.pmg = B.PMG(self.mesh, self.W0, self.sigma, self.opts, stream=stream)
+        self.iters = []
+        self.ndofs = self.mesh.ndofs
+
+    def step(self, newton):
+        s = self.stream
+        self.Wn.copy_(self.W0)
+        self.Wnm1.copy_(self.Wm1)
+        self.pmg.refresh(self.Wn, self.sigma, stream=s)
+        self.Wk.copy_(self.Wn)
+        its = 0
+        for _ in range(newton):
+            self.mesh.bdf2_rhs(self.Wk, self.Wn, self.Wnm1, self.dt, self.b, stream=s)
+            st = self.pmg.fgmres(self.Wk, self.b, self.dW, rtol=1e-5, max_restarts=4, stream=s)
+            its += st["iters"]
+            self.mesh.axpy(1.0, self.dW, self.Wk, stream=s)
+        self.iters.append(its / newton)
+        return self.Wk
+
+
+def timed_steps(torch, stepper, steps, warmup, newton, stream, flush):
+    for _ in range(warmup):
+        stepper.step(newton)
+    torch.cuda.synchronize()
+    times = []
+    stepper.iters.clear()
+    for _ in range(steps):
+        flush.zero_()                       # evict L2 between timed steps (129 MB L2)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stepper.step(newton)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def kernel_roofline(torch, B, stepper, stream, peaks):
+    """Average duration of the fine-level block-Jacobi apply (the HBM-bound
+    kernel that streams every inverse diagonal block once) and of the FP64 JVP
+    (FP64-ALU bound), each timed alone with CUDA events on the library's stream."""
+    mesh = stepper.mesh
+    E, nb = mesh.E, mesh.m * mesh.nm
+    out = {}
+    r = torch.randn_like(stepper.W0)
+    z = torch.empty_like(r)
+    n = 20
+    # block-Jacobi apply through a BJ-only handle of the same precision as the headline
+    o = B.pmg_opts((stepper.cfg["p"],), cycle=B.CYCLE_BJ, precision=stepper.opts.precision)
+    bj = B.PMG(mesh, stepper.W0, stepper.sigma, o, stream=stream)
+    for _ in range(3):
+        bj.apply(r, z, stream=stream)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        bj.apply(r, z, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    es = 4 if stepper.opts.precision == B.PREC_MIXED else 8
+    # algorithmic bytes: inverse blocks + r in + z out (+ the precision conversions of r, z)
+    blk = E * nb * nb * es
+    vec = E * nb * (es * 2 + (8 + es) * 2 if es == 4 else es * 2)
+    out["bj_apply"] = dict(ms=ms, bytes=blk + vec, gbs=(blk + vec) / (ms * 1e-3) / 1e9)
+    bj.close()
+    # FP64 exact JVP (face + volume kernels)
+    Kv = torch.empty_like(r)
+    for _ in range(3):
+        mesh.jvp(stepper.W0, r, Kv, stepper.sigma, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n):
+        mesh.jvp(stepper.W0, r, Kv, stepper.sigma, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    jb = E * nb * 8 * 3                      # read W and v, write Kv (FP64)
+    out["jvp_fp64"] = dict(ms=ms, bytes=jb, gbs=jb / (ms * 1e-3) / 1e9,
+                           hbm_frac=jb / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"])
+    return out
+
+
+def cpu_baseline_sample(cfg, newton, time_budget=40.0):
+    """The oracle, as it stands, on a bounded sample of the workload: the same
+    TGV case on a 3^3 sub-mesh (same p, physics, dt, pMG levels, tolerances),
+    one implicit step; DOFs/s of that sample."""
+    from oracle.dg import residual, jvp as ojvp, Mesh as OMesh
+    from oracle.physics import Physics
+    from oracle import solvers
+    sub = dict(cfg)
+    d = cfg["dim"]
+    sub["n"] = (3, 3, 3) if d == 3 else (3, 3, 1)
+    # the sub-mesh keeps the element size (hence dt/h) of the full mesh; the
+    # physics constants (mu, dt) are those of the full workload
+    sub["hi"] = tuple(cfg["lo"][k] + 3 * (cfg["hi"][k] - cfg["lo"][k]) / cfg["n"][k] if k < d else cfg["hi"][k]
+                      for k in range(3))
+    desc, phys = wl.mesh_desc(sub), wl.physics(cfg)
+    om = OMesh(desc["dim"], desc["n"], desc["lo"], desc["hi"], desc["p"], desc["nq1d"])
+    ph = Physics(gamma=phys["gamma"], Pr=phys["Pr"], mu=phys["mu"], Rgas=phys["Rgas"], eta=phys["eta"],
+                 roe_delta=phys["roe_delta"])
+    W0 = wl.initial_state(sub)
+    dt = wl.time_step(cfg)
+    sigma = 1.5 / dt
+    o = bench_opts(cfg)
+    t0 = time.perf_counter()
+    mg = solvers.pmg_setup(om, ph, W0, sigma, o["p_levels"], o["nu_pre"], o["nu_post"], o["nu_coarse"])
+    Wk = W0.copy()
+    its = 0
+    for _ in range(newton):
+        f = solvers.bdf2_rhs(om, residual(om, ph, Wk), Wk, W0, W0, dt)
+        x, st = solvers.fgmres(lambda z: ojvp(om, ph, Wk, z, sigma), mg, -f, rtol=1e-5, max_restarts=4)
+        its += st["iters"]
+        Wk = Wk + x
+        if time.perf_counter() - t0 > time_budget:
+            break
+    sec = time.perf_counter() - t0
+    return dict(value=om.E * om.nb / sec, unit=UNIT, cores=os.cpu_count(), kind="oracle",
+                sample="TGV p=%d on a 3^3 sub-mesh (%d DOFs, same element size, physics, dt, pMG levels), one "
+                       "implicit step (%d Newton, %d FGMRES its), %.1f s; numpy BLAS threads default to all cores"
+                       % (cfg["p"], om.E * om.nb, newton, its, sec), seconds=sec)
+
+
+def run_gb300(args):
+    import torch
+    from paper_1812_04789_gb300 import binding as B
+    from paper_1812_04789_gb300 import build as BLD
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        BLD.build()
+    if world > 1:
+        torch.distributed.barrier()
+    B.load()
+    cfg = wl.CONFIGS[args.config]
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0,
+                                                          "fallback": True}
+    stream = torch.cuda.Stream()
+    W0 = wl.initial_state(cfg)
+    Wm1 = wl.initial_state(cfg, t=-wl.time_step(cfg)) if cfg["case"] == "vortex" else W0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    results = {}
+    with torch.cuda.stream(stream):
+        clocks = Clocks(local)
+        for name, prec, steps in (("mixed", B.PREC_MIXED, args.steps), ("fp64", B.PREC_FP64, args.fp64_steps)):
+            if steps <= 0:
+                continue
+            st = Stepper(B, torch, cfg, prec, stream, W0, Wm1)
+            if name == "mixed":
+                clocks.start()
+                l0 = B.launch_count()
+            times = timed_steps(torch, st, steps, args.warmup if name == "mixed" else 1, args.newton, stream, flush)
+            if name == "mixed":
+                launches = B.launch_count() - l0
+                clk = clocks.stop()
+            tot = sum(times) / 1e3
+            if world > 1:
+                t = torch.tensor([tot], device="cuda", dtype=torch.float64)
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                tot = float(t.item())
+            results[name] = dict(ms_per_step=1e3 * tot / steps, value=world * st.ndofs * steps / tot,
+                                 fgmres_iters_per_solve=statistics.mean(st.iters), ndofs=st.ndofs,
+                                 Wfinal=st.Wk.cpu().numpy() if name in ("mixed", "fp64") else None)
+            if name == "mixed":
+                head = st
+        # mixed vs FP64 step error (same step, same inputs)
+        err = None
+        if "fp64" in results and "mixed" in results:
+            a, b = results["mixed"]["Wfinal"], results["fp64"]["Wfinal"]
+            err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        roof = kernel_roofline(torch, B, head, stream, peaks)
+        # end to end through the public API with pinned host buffers
+        e2e = None
+        if not args.no_e2e:
+            hW0 = torch.from_numpy(W0).pin_memory()
+            hWm1 = torch.from_numpy(Wm1).pin_memory()
+            hout = torch.empty_like(hW0).pin_memory()
+            n = max(1, min(args.steps, 3))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(n):
+                head.W0.copy_(hW0, non_blocking=True)
+                head.Wm1.copy_(hWm1, non_blocking=True)
+                out = head.step(args.newton)
+                hout.copy_(out, non_blocking=True)
+                stream.synchronize()
+            sec = time.perf_counter() - t0
+            e2e = {"value": world * head.ndofs * n / sec, "unit": UNIT,
+                   "h2d_bytes_per_step": int(hW0.numel() * 8 * 2), "d2h_bytes_per_step": int(hout.numel() * 8)}
+    mixed = results["mixed"]
+    bj = roof["bj_apply"]
+    es = 4
+    line = {
+        "metric": METRIC, "value": mixed["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (FP64 outer FGMRES/JVP, FP32 pMG)",
+        "data": "synthetic (closed-form Taylor-Green initial state, L2-projected)",
+        "config": {"workload": "%s: TGV %dx%dx%d hex, p=%d, Re=%g, M=%g, BDF2 dt=%g t_c, pMG %s FMG "
+                               "nu=10/10/30, FGMRES(30) rtol 1e-5, %d Newton/step"
+                               % (args.config, *cfg["n"], cfg["p"], cfg["Re"], cfg["M"], cfg["dt_conv"],
+                                  "-".join(map(str, cfg["p_levels"])), args.newton),
+                   "dofs": mixed["ndofs"], "l2": "256 MB buffer written between timed steps",
+                   "parallelism": "replicas (one independent case per GPU)"},
+        "fp64": {"value": results.get("fp64", {}).get("value"),
+                 "ms_per_step": results.get("fp64", {}).get("ms_per_step"),
+                 "fgmres_iters_per_solve": results.get("fp64", {}).get("fgmres_iters_per_solve")},
+        "fgmres_iters_per_solve": mixed["fgmres_iters_per_solve"],
+        "mixed_vs_fp64_rel_l2": err,
+        "roofline": {"bound": "hbm", "kernel": "bsr_kernel<float> (fine block-Jacobi apply)",
+                     "achieved": bj["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": bj["gbs"] / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": "of fallback" if peaks.get("fallback") else "of measured (MEASURED_PEAKS.json hbm_gbs)",
+                     "ms": bj["ms"], "algorithmic_bytes": bj["bytes"]},
+        "jvp_fp64": roof["jvp_fp64"],
+        "clocks": clk, "gpu_launches": launches, "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline_sample(cfg, args.newton).items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cfg = wl.CONFIGS[args.config]
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline_sample(cfg, args.newton)
+        if i >= args.warmup:
+            times.append(r["seconds"])
+            samples.append(r)
+    dofs = samples[0]["value"] * samples[0]["seconds"]
+    value = dofs * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (closed-form Taylor-Green initial state, L2-projected)",
+            "config": {"workload": "%s sampled on a 3^3 sub-mesh (CPU oracle)" % args.config},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -136,6 +136,13 @@ typedef struct {
 dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, const dg_pmg_opts* opts,
                        void* stream, dg_pmg* out);
 
+/* Recompute the preconditioner of an existing handle at a new state W and
+ * shift sigma (same mesh and options), in the handle's own buffers: the same
+ * work as dg_pmg_setup without allocation, asynchronous on `stream` (a
+ * singular block is reported by dg_status_sync).  This is the once-per-time-
+ * step preconditioner update of a lagged (Sec. 7.4) implicit time loop. */
+dg_status dg_pmg_refresh(dg_pmg pmg, const double* W, double sigma, void* stream);
+
 /* z = P^{-1} r: one application of the preconditioner (MG_full of Algorithm 1,
  * one MG_V of Algorithm 2, or block Jacobi), r and z device FP64, may not alias. */
 dg_status dg_pmg_apply(dg_pmg pmg, const double* r, double* z, void* stream);

@@ -22,7 +22,7 @@ BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR = 0, 1
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
-            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count"]
+            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh"]
 
 
 class DGError(RuntimeError):
@@ -89,6 +89,7 @@ def load(path=None):
         "dg_bdf2_rhs": [P, P, P, P, ctypes.c_double, P, P],
         "dg_axpy": [P, ctypes.c_double, P, P, P],
         "dg_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
+        "dg_pmg_refresh": [P, P, ctypes.c_double, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -231,6 +232,11 @@ class PMG:
 
     __del__ = close
 
+    def refresh(self, W, sigma, stream=None):
+        """Recompute the preconditioner at (W, sigma) in the handle's buffers (async)."""
+        _check("dg_pmg_refresh", load().dg_pmg_refresh(self.h, _ptr(W), float(sigma), _stream(stream)))
+        self.sigma = sigma
+
     def apply(self, r, z, stream=None):
         _check("dg_pmg_apply", load().dg_pmg_apply(self.h, _ptr(r), _ptr(z), _stream(stream)))
 
@@ -257,3 +263,4 @@ class PMG:
         if raise_on_error and code != DG_OK:
             raise DGError("dg_fgmres_step", code)
         return out
+

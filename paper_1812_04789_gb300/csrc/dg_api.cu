@@ -166,30 +166,22 @@ static cudaError_t dalloc(std::vector<void*>& list, void** p, size_t bytes, size
 }
 
 template <class T>
-static dg_status setup_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t st) {
+static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
   const Mesh& M = h->mesh->m;
   const dg_pmg_opts& o = h->opts;
   mg.mesh = &M;
-  mg.sigma = (T)h->sigma;
   mg.nu_coarse = o.nu_coarse;
   mg.cycle = o.cycle;
   const int nl = o.cycle == DG_CYCLE_BJ ? 1 : o.n_levels;
   mg.lv.resize(nl);
   const long N0 = (long)M.E * M.nb;
   CK(dalloc(mg.allocs, (void**)&mg.W, sizeof(T) * N0, &h->vector_bytes));
-  if (std::is_same<T, double>::value)
-    CK(cudaMemcpyAsync(mg.W, W64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
-  else
-    CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
   for (int l = 0; l < nl; ++l) {
     Level<T>& L = mg.lv[l];
     L.p = o.p_level[l];
-    L.nm = 1;
-    {
-      long c = 1;  // C(p + d, d)
-      for (int i = 1; i <= M.d; ++i) c = c * (L.p + i) / i;
-      L.nm = (int)c;
-    }
+    long c = 1;  // n_m = C(p + d, d)
+    for (int i = 1; i <= M.d; ++i) c = c * (L.p + i) / i;
+    L.nm = (int)c;
     L.nb = M.m * L.nm;
     L.N = (long)M.E * L.nb;
     L.nu_pre = o.nu_pre[l];
@@ -207,20 +199,34 @@ static dg_status setup_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t s
       h->vector_bytes += L.kr.bytes();
     }
   }
-  // blocks: fine diagonal (+ neighbour blocks at the first coarse order)
+  // probing caches live in global memory when they exceed shared memory
   bool fits = true;
   size_t tot = probe_scratch_elems<T>(M, nl > 1 ? mg.lv[1].nm : 0, &fits);
-  T* scratch = nullptr;
-  size_t scratch_elems = 0;
   if (!fits) {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    scratch_elems = tot * (size_t)std::min(M.E, 2 * nsm);
-    CK(dalloc(mg.allocs, (void**)&scratch, sizeof(T) * scratch_elems, nullptr));
+    mg.scratch_elems = tot * (size_t)std::min(M.E, 2 * nsm);
+    CK(dalloc(mg.allocs, (void**)&mg.scratch, sizeof(T) * mg.scratch_elems, &h->block_bytes));
   }
+  return DG_OK;
+}
+
+// Preconditioner at state W and shift sigma into the allocated handle: fine
+// diagonal blocks (+ neighbour blocks at the first coarse order) by probing,
+// coarse blocks by truncation (inheritance), block inverses.  Asynchronous.
+template <class T>
+static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t st) {
+  const Mesh& M = h->mesh->m;
+  const int nl = (int)mg.lv.size();
+  const long N0 = (long)M.E * M.nb;
+  mg.sigma = (T)h->sigma;
+  if (std::is_same<T, double>::value)
+    CK(cudaMemcpyAsync(mg.W, W64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
+  else
+    CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
   CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, nl > 1 ? mg.lv[1].O : nullptr,
-                            nl > 1 ? mg.lv[1].nm : 0, scratch, scratch_elems, st));
+                            nl > 1 ? mg.lv[1].nm : 0, mg.scratch, mg.scratch_elems, st));
   for (int l = 1; l < nl; ++l) {
     Level<T>& L = mg.lv[l];
     CK(launch_truncate_blocks<T>(mg.lv[0].Dinv, mg.lv[0].nm, L.Dop, L.nm, M.m, M.E, st));
@@ -229,11 +235,6 @@ static dg_status setup_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t s
     CK(cudaMemcpyAsync(L.Dinv, L.Dop, sizeof(T) * (size_t)M.E * L.nb * L.nb, cudaMemcpyDeviceToDevice, st));
   }
   for (int l = 0; l < nl; ++l) CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, M.E, M.status, st));
-  CK(cudaStreamSynchronize(st));
-  if (scratch) {
-    cudaFree(scratch);
-    mg.allocs.erase(std::find(mg.allocs.begin(), mg.allocs.end(), (void*)scratch));
-  }
   return DG_OK;
 }
 
@@ -315,8 +316,13 @@ extern "C" dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, c
   h->sigma = sigma;
   h->precision = opts->precision;
   CK(cudaMemsetAsync(mesh->m.status, 0, sizeof(int), st));
-  if (h->precision == DG_PREC_FP64) s = setup_mg<double>(h, h->mg64, W, st);
-  else s = setup_mg<float>(h, h->mg32, W, st);
+  if (h->precision == DG_PREC_FP64) {
+    s = alloc_mg<double>(h, h->mg64);
+    if (s == DG_OK) s = compute_mg<double>(h, h->mg64, W, st);
+  } else {
+    s = alloc_mg<float>(h, h->mg32);
+    if (s == DG_OK) s = compute_mg<float>(h, h->mg32, W, st);
+  }
   const long N0 = (long)mesh->m.E * mesh->m.nb;
   if (s == DG_OK && h->precision == DG_PREC_MIXED) {
     if (dalloc(h->allocs, (void**)&h->r32, sizeof(float) * N0, &h->vector_bytes) != cudaSuccess ||
@@ -347,6 +353,15 @@ extern "C" dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, c
   }
   *out = h;
   return DG_OK;
+}
+
+extern "C" dg_status dg_pmg_refresh(dg_pmg h, const double* W, double sigma, void* stream) {
+  if (!h || !W || !(sigma >= 0.0)) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->sigma = sigma;
+  dg_status s = h->precision == DG_PREC_FP64 ? compute_mg<double>(h, h->mg64, W, st)
+                                             : compute_mg<float>(h, h->mg32, W, st);
+  return s;
 }
 
 static dg_status pmg_apply_impl(dg_pmg h, const double* r, double* z, cudaStream_t st) {

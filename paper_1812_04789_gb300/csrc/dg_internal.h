@@ -140,6 +140,8 @@ struct MG {
   T sigma = 0;
   int nu_coarse = 0;
   int cycle = 0;
+  T* scratch = nullptr;      // probing caches in global memory (large blocks only)
+  size_t scratch_elems = 0;
   std::vector<void*> allocs;
   cudaError_t op(int l, const T* x, T* y, cudaStream_t st);
   cudaError_t smooth(int l, const T* b, T* x, int nu, cudaStream_t st);
