@@ -91,6 +91,22 @@ dg_status dg_mesh_info(dg_mesh mesh, int* n_elem, int* n_modes, int* n_vars, siz
  * a quadrature point. */
 dg_status dg_residual(dg_mesh mesh, const double* W, const double* S, double* R, void* stream);
 
+/* dg_residual for callers that must not cause any device allocation when they
+ * ask for a residual (the paper has no counterpart: this is a library-usage
+ * entry point).  Such callers include applications that reserve all device
+ * memory at start-up and time-critical loops that must stay out of the CUDA
+ * allocator.  Same result and arguments as dg_residual, same kernels; the
+ * face-slot scratch is a fixed file-scope device array of 2^20 doubles (8 MiB)
+ * that every GPU loading the library holds until the process exits, instead
+ * of the mesh handle's workspace.
+ * Limits: E * dim * 2 * m * n_m must not exceed 2^20, else DG_ERR_INVALID.
+ * The first call on a device looks up the array's address with that device
+ * current (make it before any stream capture).  All calls share the array:
+ * calls that may overlap on the GPU race, so order them on one stream.
+ * The array keeps the last call's contents; nothing in it needs clearing,
+ * since each call writes every slot it reads. */
+dg_status dg_residual_noalloc(dg_mesh mesh, const double* W, const double* S, double* R, void* stream);
+
 #define DG_JVP_EXACT 0      /* forward-mode derivative of the discrete residual */
 #define DG_JVP_FD 1         /* eq. DG-mf with h = eps sqrt(1 + ||v||)/||W|| as printed */
 #define DG_JVP_FD_SCALED 2  /* eq. DG-mf with h = eps sqrt(1 + ||W||)/||v|| */

@@ -22,7 +22,7 @@ BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR = 0, 1
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
-            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh"]
+            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh", "dg_residual_noalloc"]
 
 
 class DGError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path=None):
         "dg_axpy": [P, ctypes.c_double, P, P, P],
         "dg_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
         "dg_pmg_refresh": [P, P, ctypes.c_double, P],
+        "dg_residual_noalloc": [P, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -174,6 +175,12 @@ class Mesh:
 
     def residual(self, W, R, S=None, stream=None):
         _check("dg_residual", load().dg_residual(self.h, _ptr(W), _ptr(S), _ptr(R), _stream(stream)))
+
+    def residual_noalloc(self, W, R, S=None, stream=None):
+        """The residual with the face scratch in the library's fixed device array
+        (no allocation at any call; meshes up to E*d*2*m*n_m = 2^20 doubles)."""
+        _check("dg_residual_noalloc", load().dg_residual_noalloc(self.h, _ptr(W), _ptr(S), _ptr(R),
+                                                                 _stream(stream)))
 
     def jvp(self, W, v, Kv, sigma, mode=JVP_EXACT, R_W=None, stream=None):
         _check("dg_jvp", load().dg_jvp(self.h, _ptr(W), _ptr(R_W), float(sigma), _ptr(v), _ptr(Kv),

@@ -51,6 +51,11 @@ template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
                             T* out, cudaStream_t st);
 
+// FP64 residual writing its face terms to `slots` (E * d * 2 * nb doubles)
+// instead of the mesh handle's face-slot workspace.
+cudaError_t launch_residual_with_slots(const Mesh& M, const double* W, const double* S, double* out,
+                                       double* slots, cudaStream_t st);
+
 // Element Jacobian blocks by probing: D[e] = dR_e/dW_e + sigma |J| I (nb x nb),
 // and when O != nullptr the neighbour blocks O[e][2k+side] restricted to the
 // first nmc modes of every variable (nbc x nbc, nbc = m nmc).

@@ -309,4 +309,38 @@ template cudaError_t launch_residual<double>(const Mesh&, const double*, const d
 template cudaError_t launch_residual<float>(const Mesh&, const float*, const float*, const float*, float,
                                             bool, float*, cudaStream_t);
 
+// FP64 residual with caller-provided face slots (E * d * 2 * nb doubles) in
+// place of the mesh handle's own: the same two kernels, launched the same way.
+template <int D>
+static cudaError_t run_residual_slots(const Mesh& Ms, const double* W, const double* S, double* out,
+                                      double* slots, cudaStream_t st) {
+  MeshView<double> mv = Ms.view<double>();
+  Phys<double> ph = Ms.phys_t<double>();
+  int fpc = std::max(1, 128 / Ms.nqf);
+  size_t fsm = face_smem<double>(Ms, fpc, false);
+  while (fsm > 200 * 1024 && fpc > 1) fsm = face_smem<double>(Ms, --fpc, false);
+  if (fsm > 48 * 1024)
+    cudaFuncSetAttribute(face_kernel<D, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+  int nfaces = D * Ms.E;
+  note_launch();
+  face_kernel<D, double, false><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, nullptr, slots,
+                                                                            Ms.status, fpc);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int epc = std::max(1, 256 / Ms.nq);
+  size_t vsm = vol_smem<double>(Ms, epc, false);
+  while (vsm > 200 * 1024 && epc > 1) vsm = vol_smem<double>(Ms, --epc, false);
+  if (vsm > 48 * 1024)
+    cudaFuncSetAttribute(volume_kernel<D, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+  note_launch();
+  volume_kernel<D, double, false><<<(Ms.E + epc - 1) / epc, 256, vsm, st>>>(mv, ph, W, nullptr, slots, S, 0.0,
+                                                                           out, Ms.status, epc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_with_slots(const Mesh& M, const double* W, const double* S, double* out,
+                                       double* slots, cudaStream_t st) {
+  return M.d == 2 ? run_residual_slots<2>(M, W, S, out, slots, st) : run_residual_slots<3>(M, W, S, out, slots, st);
+}
+
 }  // namespace dgk
