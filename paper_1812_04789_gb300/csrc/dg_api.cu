@@ -1,6 +1,7 @@
 // C ABI: residual, JVP, p-multigrid setup/apply and the FGMRES implicit-step
 // solve (Sec. 5.1, Sec. 6 with Algorithms 1-2, Sec. 6.1, Sec. 6.3, Sec. 7.4).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -273,6 +274,37 @@ extern "C" dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, do
   return DG_OK;
 }
 
+// Capture one preconditioner application (every level, every smoother
+// iteration: a few thousand small launches) as a CUDA graph on fixed staging
+// buffers.  The graph reads the handle's blocks and state through pointers, so
+// dg_pmg_refresh does not invalidate it.  DG_PMG_NO_GRAPH=1 disables it.
+static dg_status capture_apply_graph(dg_pmg h) {
+  const char* env = getenv("DG_PMG_NO_GRAPH");
+  if (env && env[0] == '1') return DG_OK;
+  const long N0 = (long)h->mesh->m.E * h->mesh->m.nb;
+  if (h->precision == DG_PREC_FP64) {
+    if (dalloc(h->allocs, (void**)&h->r64, sizeof(double) * N0, &h->vector_bytes) != cudaSuccess ||
+        dalloc(h->allocs, (void**)&h->z64, sizeof(double) * N0, &h->vector_bytes) != cudaSuccess)
+      return DG_ERR_OOM;
+  }
+  CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  unsigned long long l0 = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED);
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = h->precision == DG_PREC_FP64 ? h->mg64.apply(h->r64, h->z64, h->cap_stream)
+                                               : h->mg32.apply(h->r32, h->z32, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return DG_ERR_CUDA;
+  }
+  h->graph = g;
+  h->graph_kernels = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED) - l0;
+  __atomic_fetch_sub(&launch_counter(), h->graph_kernels, __ATOMIC_RELAXED);   // captured, not run
+  CK(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+  return DG_OK;
+}
+
 static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
   if (o->cycle != DG_CYCLE_FMG && o->cycle != DG_CYCLE_V && o->cycle != DG_CYCLE_BJ) return DG_ERR_INVALID;
   if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
@@ -290,6 +322,9 @@ static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
 
 extern "C" dg_status dg_pmg_destroy(dg_pmg h) {
   if (!h) return DG_ERR_INVALID;
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   free_mg(h->mg64);
   free_mg(h->mg32);
   h->outer.release();
@@ -347,6 +382,7 @@ extern "C" dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, c
     else if (hs & ST_NONPHYSICAL)
       s = DG_ERR_NONPHYSICAL;
   }
+  if (s == DG_OK) s = capture_apply_graph(h);
   if (s != DG_OK) {
     dg_pmg_destroy(h);
     return s;
@@ -366,6 +402,20 @@ extern "C" dg_status dg_pmg_refresh(dg_pmg h, const double* W, double sigma, voi
 
 static dg_status pmg_apply_impl(dg_pmg h, const double* r, double* z, cudaStream_t st) {
   const long N0 = (long)h->mesh->m.E * h->mesh->m.nb;
+  if (h->graph_exec) {
+    // replay the captured application between fixed staging buffers
+    if (h->precision == DG_PREC_FP64) {
+      CK(cudaMemcpyAsync(h->r64, r, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
+      CK(cudaGraphLaunch(h->graph_exec, st));
+      CK(cudaMemcpyAsync(z, h->z64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
+    } else {
+      CK(launch_convert<double, float>(N0, r, h->r32, st));
+      CK(cudaGraphLaunch(h->graph_exec, st));
+      CK(launch_convert<float, double>(N0, h->z32, z, st));
+    }
+    __atomic_fetch_add(&launch_counter(), h->graph_kernels, __ATOMIC_RELAXED);
+    return DG_OK;
+  }
   if (h->precision == DG_PREC_FP64) {
     CK(h->mg64.apply(r, z, st));
   } else {

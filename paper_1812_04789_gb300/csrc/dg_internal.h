@@ -23,6 +23,7 @@ struct Tables {
   T *vphiT = nullptr, *vdphiT = nullptr, *vphi = nullptr, *vdphi = nullptr, *vw = nullptr;
   T *fphiT = nullptr, *fdphiT = nullptr, *fphi = nullptr, *fdphi = nullptr, *fw = nullptr;
   T* lift = nullptr;
+  T* liftT = nullptr;        // lifted test tables [2d][2][nqf][nm]
   T* slots = nullptr;        // face slots [E][d][2][nb]
   T* fd_w = nullptr;         // finite-difference JVP scratch: W + h v
   T* fd_r = nullptr;         // finite-difference JVP scratch: R(W + h v)
@@ -173,6 +174,14 @@ struct dg_pmg_s {
   dgk::Krylov<double> outer; // FGMRES workspace (allocated at first solve)
   int outer_restart = 0;
   double* tmp64 = nullptr;
+  double* r64 = nullptr;     // FP64 staging of the preconditioner input/output
+  double* z64 = nullptr;
+  // the whole preconditioner application, captured once as a CUDA graph on
+  // fixed staging buffers and replayed on the caller's stream
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  unsigned long long graph_kernels = 0;
   std::vector<void*> allocs;
   size_t block_bytes = 0, vector_bytes = 0;
 };
