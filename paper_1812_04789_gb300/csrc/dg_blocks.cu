@@ -1,17 +1,23 @@
 // Element Jacobian blocks, subspace inheritance and block Jacobi
 // (Sec. 5.1 eq. ODEDG; Sec. 6.1 inheritance; Sec. 6.3 element block Jacobi).
 //
-// probe_kernel: one CTA per element (grid-stride).  The element's and its 2d
-// neighbours' traces are computed once; then for every local unit direction
-// e_j (variable w, mode i) the pointwise physics is evaluated in dual numbers
-// with the tangent phi_i (grad phi_i) in component w, and projected onto all
-// test functions: column j of dR_e/dW_e.  Faces are evaluated from the
-// element's own side (each interior face twice over the mesh), so no face
-// slots are needed.  Neighbour blocks dR_e/dW_nbr take the seed on the
-// neighbour's trace instead, for the first nmc modes only (Sec. 6.3: at
-// coarse order).  A direction with a single element makes the element its own
-// neighbour: the seed then sits on both traces and the coupling belongs to
-// the diagonal block (the neighbour block is zero).
+// probe_kernel: one CTA per element (grid-stride).  The diagonal block
+//   D_e[(v,i'),(w,i)] = dR_{e,v,i'}/dW_{e,w,i} + sigma |J| delta
+// is a sum over the element's volume points and the points of its own faces of
+//   Test_c(p, i') * J_p[(v,c),(w,s)] * Trial_s(p, i),
+// where J_p is the pointwise derivative of the point outputs c (volume: the flux
+// tensor F[v][k]; face: the numerical flux, the two lifting integrands and the
+// dual-consistency tensor) with respect to the point inputs s of variable w
+// (the value and the d gradient components), Trial_s is the basis value or
+// gradient, and Test_c the matching test function (the BR2 lifting is linear,
+// so it is folded into precomputed lifted test functions).  For each w the
+// kernel takes chunks of points: (J) 1+d dual-number evaluations per point,
+// (Y) Y = J . Trial, (G) a register-tiled accumulation of Test . Y into the
+// block in global memory (each CTA owns its element's blocks: no atomics).
+// Neighbour blocks dR_e/dW_nbr (first nmc modes only, Sec. 6.3: coarse order)
+// use the same machinery with the seed on the neighbour's trace.  A direction
+// with one element makes the element its own neighbour: the neighbour-side
+// seed of such a face then adds to the diagonal block.
 #include <algorithm>
 #include <type_traits>
 
@@ -19,23 +25,36 @@
 
 namespace dgk {
 
+constexpr int PROBE_QC = 8;    // points per contraction sub-chunk
+constexpr int PROBE_CH = 8;    // columns per register tile
+template <class T> struct ProbeJQC { static constexpr int value = 64; };   // points per Jacobian chunk
+template <> struct ProbeJQC<double> { static constexpr int value = 32; };
+constexpr int PROBE_RI = 4;    // test rows per register tile
+
+__host__ __device__ inline size_t probe_align4(size_t x) { return (x + 3) & ~size_t(3); }
+__host__ __device__ inline int probe_pad(int n) { return (n + PROBE_CH - 1) / PROBE_CH * PROBE_CH; }
+
+// Per-CTA cache layout (elements of T; every buffer starts on a multiple of 4
+// elements, so 16-byte vector loads of the tiles are aligned)
 template <class T>
 struct ProbeLayout {
-  size_t cW, cU, cFU, bF, bG, bFp, bDo, total;
-  __host__ __device__ ProbeLayout(int D, int nb, int nq, int nqf) {
-    int M = D + 2, nf = 2 * D;
+  size_t cW, cU, cFU, Jb, Yb, Tb, total;
+  __host__ __device__ ProbeLayout(int D, int nb, int nm, int nq, int nqf) {
+    const int M = D + 2, nf = 2 * D, KM = 3 + D, nmp = probe_pad(nm);
     size_t o = 0;
-    cW = o;  o += (size_t)(1 + nf) * nb;
-    cU = o;  o += (size_t)nq * M * (1 + D);
-    cFU = o; o += (size_t)nf * 2 * nqf * M * (1 + D);
-    bF = o;  o += (size_t)nq * M * D;
-    bG = o;  o += (size_t)nf * 2 * nqf * M;
-    bFp = o; o += (size_t)nf * nqf * M;
-    bDo = o; o += (size_t)nf * nqf * M * D;
+    cW = o;  o = probe_align4(o + (size_t)(1 + nf) * nb);
+    cU = o;  o = probe_align4(o + (size_t)nq * M * (1 + D));
+    cFU = o; o = probe_align4(o + (size_t)nf * 2 * nqf * M * (1 + D));
+    Jb = o;  o = probe_align4(o + (size_t)ProbeJQC<T>::value * (1 + D) * M * KM);
+    Yb = o;  o = probe_align4(o + (size_t)PROBE_QC * M * KM * nmp);
+    Tb = o;  o = probe_align4(o + (size_t)PROBE_QC * KM * nmp);
     total = o;
   }
 };
 
+// Tangent of the face-point outputs for a unit seed: so/sgo on the own trace,
+// sn/sgn on the neighbour's.  Outputs: numerical flux fp[v], lifting integrands
+// GL[v], GR[v] of the face's +k / -k sides, and the element's own dual tensor.
 template <int D, class T>
 __device__ __forceinline__ void face_point_tangent(const T* pu_own, const T* pu_nb, int k, int side,
                                                    int w, T so, const T* sgo, T sn, const T* sgn,
@@ -43,7 +62,6 @@ __device__ __forceinline__ void face_point_tangent(const T* pu_own, const T* pu_
                                                    T* bDo) {
   using S = Dual<T>;
   constexpr int M = D + 2;
-  // pu_*: primal [M] then grad [M][D]; seeds so/sgo on own trace, sn/sgn on the neighbour's
   S uo[M], un[M], go[M][D], gn[M][D];
 #pragma unroll
   for (int v = 0; v < M; ++v) {
@@ -70,28 +88,234 @@ __device__ __forceinline__ void face_point_tangent(const T* pu_own, const T* pu_
   }
 }
 
+enum ProbeTask : int { TASK_VOL = 0, TASK_FACE_OWN = 1, TASK_FACE_NBR = 2 };
+
+template <class T>
+struct ProbeCtx {
+  MeshView<T> mv;
+  Phys<T> ph;
+  T half_eta;
+  const T* cU;
+  const T* cFU;
+  T* Jb;
+  T* Yb;
+  T* Tb;
+};
+
+// 16-byte vector loads of N consecutive elements (aligned by construction)
+template <int N>
+__device__ __forceinline__ void vload(const float* p, float* out) {
+#pragma unroll
+  for (int j = 0; j < N; j += 4) {
+    float4 x = *reinterpret_cast<const float4*>(p + j);
+    out[j] = x.x; out[j + 1] = x.y; out[j + 2] = x.z; out[j + 3] = x.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void vload(const double* p, double* out) {
+#pragma unroll
+  for (int j = 0; j < N; j += 2) {
+    double2 x = *reinterpret_cast<const double2*>(p + j);
+    out[j] = x.x; out[j + 1] = x.y;
+  }
+}
+
+// One sweep: points [0, npts) of a task, seed variable w, accumulated into the
+// target block rows (v, i' < nmo) x columns (w, i < nmi), leading dimension ld.
+template <int D, class T>
+__device__ __forceinline__ void probe_sweep(const ProbeCtx<T>& cx, int task, int sface, int npts, int w, int nmo,
+                                            int nmi, T* __restrict__ tgt, int ld) {
+  constexpr int M = D + 2, KM = 3 + D, PU = M * (1 + D), NS = 1 + D;
+  constexpr int JQC = ProbeJQC<T>::value;
+  const MeshView<T>& mv = cx.mv;
+  const int nm = mv.nm, nq = mv.nq, nqf = mv.nqf;
+  const int nk = task == TASK_VOL ? D : KM;
+  const int nmp = probe_pad(nmi);
+  T* Jb = cx.Jb;
+  T* Yb = cx.Yb;
+  T* Tb = cx.Tb;
+  for (int cj = 0; cj < npts; cj += JQC) {
+    const int ncj = min(JQC, npts - cj);
+    // (J) pointwise derivatives for the 1+d unit seeds of variable w
+    for (int t = threadIdx.x; t < ncj * NS; t += blockDim.x) {
+      const int pl = t / NS, sd = t % NS, pt = cj + pl;
+      T* jo = Jb + ((size_t)pl * NS + sd) * M * KM;
+      if (task == TASK_VOL) {
+        using S = Dual<T>;
+        const T* pu = cx.cU + (size_t)pt * PU;
+        S u[M], g[M][D], F[M][D];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          u[v] = S(pu[v], (v == w && sd == 0) ? T(1) : T(0));
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) g[v][kk] = S(pu[M + v * D + kk], (v == w && sd == 1 + kk) ? T(1) : T(0));
+        }
+        flux_total<D, S, T>(u, g, F, cx.ph);
+#pragma unroll
+        for (int v = 0; v < M; ++v)
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) jo[v * KM + kk] = F[v][kk].d;
+      } else {
+        const int s = task == TASK_FACE_OWN ? pt / nqf : sface;
+        const int q = task == TASK_FACE_OWN ? pt % nqf : pt;
+        const bool own = task == TASK_FACE_OWN;
+        T sgo[D], sgn[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) {
+          sgo[kk] = (own && sd == 1 + kk) ? T(1) : T(0);
+          sgn[kk] = (!own && sd == 1 + kk) ? T(1) : T(0);
+        }
+        T oGL[M], oGR[M], oFp[M], oDo[M * D];
+        face_point_tangent<D, T>(cx.cFU + ((size_t)(s * 2) * nqf + q) * PU, cx.cFU + ((size_t)(s * 2 + 1) * nqf + q) * PU,
+                                 s / 2, s % 2, w, (own && sd == 0) ? T(1) : T(0), sgo, (!own && sd == 0) ? T(1) : T(0),
+                                 sgn, cx.ph, oGL, oGR, oFp, oDo);
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          jo[v * KM + 0] = oFp[v];
+          jo[v * KM + 1] = oGL[v];
+          jo[v * KM + 2] = oGR[v];
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) jo[v * KM + 3 + kk] = oDo[v * D + kk];
+        }
+      }
+    }
+    __syncthreads();
+    for (int c0 = cj; c0 < cj + ncj; c0 += PROBE_QC) {
+      const int nc = min(PROBE_QC, cj + ncj - c0);
+      // (Y) contraction with the trial functions of the seeded trace, and the
+      // test functions of the sub-chunk's points (independent of v and w);
+      // rows are padded to a multiple of PROBE_CH with zeros
+      // one warp per (point, output kind) row; the lanes run over the modes and
+      // produce Y for every variable v at once (the trial values are shared)
+      const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+      for (int row = threadIdx.x >> 5; row < nc * nk; row += nwarp) {
+        const int pl = row / nk, kind = row - pl * nk, pt = c0 + pl;
+        T jv[M][NS];
+#pragma unroll
+        for (int v = 0; v < M; ++v)
+#pragma unroll
+          for (int sd = 0; sd < NS; ++sd) jv[v][sd] = Jb[((size_t)(pt - cj) * NS + sd) * M * KM + v * KM + kind];
+        int f = 0, s = 0, q = pt;
+        T tscale = T(0);
+        const T* trow = nullptr;
+        if (task == TASK_VOL) {
+          tscale = -mv.vw[pt];
+          trow = mv.vdphi + ((size_t)kind * nq + pt) * nm;
+        } else {
+          s = task == TASK_FACE_OWN ? pt / nqf : sface;
+          q = task == TASK_FACE_OWN ? pt % nqf : pt;
+          f = task == TASK_FACE_OWN ? s : (s ^ 1);
+          // test functions live on the element's own face s
+          const T sg = (s % 2) ? T(1) : T(-1);
+          const T fwq = mv.fw[(size_t)(s / 2) * nqf + q];
+          if (kind == 0) {
+            tscale = sg * fwq;
+            trow = mv.fphi + ((size_t)s * nqf + q) * nm;
+          } else if (kind < 3) {
+            tscale = sg * cx.half_eta;
+            trow = mv.liftT + (((size_t)s * 2 + (kind - 1)) * nqf + q) * nm;
+          } else {
+            tscale = -fwq;
+            trow = mv.fdphi + (((size_t)s * D + (kind - 3)) * nqf + q) * nm;
+          }
+        }
+        for (int i = lane; i < nmp; i += 32) {
+          T phi[NS];
+          T test = T(0);
+          if (i < nmi) {
+            if (task == TASK_VOL) {
+              phi[0] = mv.vphi[(size_t)pt * nm + i];
+#pragma unroll
+              for (int kk = 0; kk < D; ++kk) phi[1 + kk] = mv.vdphi[((size_t)kk * nq + pt) * nm + i];
+            } else {
+              phi[0] = mv.fphi[((size_t)f * nqf + q) * nm + i];
+#pragma unroll
+              for (int kk = 0; kk < D; ++kk) phi[1 + kk] = mv.fdphi[(((size_t)f * D + kk) * nqf + q) * nm + i];
+            }
+            test = tscale * trow[i];
+          } else {
+#pragma unroll
+            for (int sd = 0; sd < NS; ++sd) phi[sd] = T(0);
+          }
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            T y = T(0);
+#pragma unroll
+            for (int sd = 0; sd < NS; ++sd) y += jv[v][sd] * phi[sd];
+            Yb[(((size_t)pl * M + v) * nk + kind) * nmp + i] = y;
+          }
+          Tb[((size_t)pl * nk + kind) * nmp + i] = test;
+        }
+      }
+      __syncthreads();
+      // (G) tgt[(v,i'),(w,i)] += sum_{points, kinds} Test(p, kind, i') Y[p][v][kind][i],
+      // each thread a PROBE_RI x PROBE_CH register tile
+      const int nch = nmp / PROBE_CH, nib = (nmo + PROBE_RI - 1) / PROBE_RI;
+      for (int t = threadIdx.x; t < M * nib * nch; t += blockDim.x) {
+        const int ch = t % nch, r = t / nch, ib = r % nib, v = r / nib;
+        const int i0 = ch * PROBE_CH, ip0 = ib * PROBE_RI;
+        T acc[PROBE_RI][PROBE_CH];
+#pragma unroll
+        for (int a = 0; a < PROBE_RI; ++a)
+#pragma unroll
+          for (int c = 0; c < PROBE_CH; ++c) acc[a][c] = T(0);
+        for (int pl = 0; pl < nc; ++pl) {
+          for (int kind = 0; kind < nk; ++kind) {
+            T tv[PROBE_RI], yv[PROBE_CH];
+            vload<PROBE_RI>(Tb + ((size_t)pl * nk + kind) * nmp + ip0, tv);
+            vload<PROBE_CH>(Yb + (((size_t)pl * M + v) * nk + kind) * nmp + i0, yv);
+#pragma unroll
+            for (int a = 0; a < PROBE_RI; ++a)
+#pragma unroll
+              for (int c = 0; c < PROBE_CH; ++c) acc[a][c] += tv[a] * yv[c];
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < PROBE_RI; ++a) {
+          const int ip = ip0 + a;
+          if (ip < nmo) {
+            T* row = tgt + (size_t)(v * nmo + ip) * ld + (size_t)w * nmi + i0;
+#pragma unroll
+            for (int c = 0; c < PROBE_CH; ++c)
+              if (i0 + c < nmi) row[c] += acc[a][c];
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <int D, class T>
 __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, const T* __restrict__ W,
                                                     T sigma, T* __restrict__ Dout, T* __restrict__ Oout,
                                                     int nmc, T* gscratch, int use_smem, int* status) {
-  constexpr int M = D + 2, NF = 2 * D;
+  constexpr int M = D + 2, NF = 2 * D, PU = M * (1 + D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = mv.nb, nm = mv.nm, nq = mv.nq, nqf = mv.nqf, E = mv.E;
-  ProbeLayout<T> L(D, nb, nq, nqf);
+  const ProbeLayout<T> L(D, nb, nm, nq, nqf);
   T* C = use_smem ? reinterpret_cast<T*>(smem_raw) : gscratch + (size_t)blockIdx.x * L.total;
   T* cW = C + L.cW;
   T* cU = C + L.cU;
   T* cFU = C + L.cFU;
-  T* bF = C + L.bF;
-  T* bG = C + L.bG;
-  T* bFp = C + L.bFp;
-  T* bDo = C + L.bDo;
-  const int PU = M * (1 + D);
+  ProbeCtx<T> cx;
+  cx.mv = mv;
+  cx.ph = ph;
+  cx.half_eta = T(0.5) * ph.eta;
+  cx.cU = cU;
+  cx.cFU = cFU;
+  cx.Jb = C + L.Jb;
+  cx.Yb = C + L.Yb;
+  cx.Tb = C + L.Tb;
   const int nbc = M * nmc;
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
     int nbrs[NF];
 #pragma unroll
     for (int s = 0; s < NF; ++s) nbrs[s] = mv.nbr[e * NF + s];
+    T* De = Dout + (size_t)e * nb * nb;
+    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) De[t] = (t / nb == t % nb) ? sigma * mv.detJ : T(0);
+    if (Oout)
+      for (int t = threadIdx.x; t < NF * nbc * nbc; t += blockDim.x) Oout[(size_t)e * NF * nbc * nbc + t] = T(0);
     // ---- stage W of the element and its neighbours (face order s = 2k + side)
     for (int t = threadIdx.x; t < (1 + NF) * nb; t += blockDim.x) {
       int who = t / nb, j = t % nb;
@@ -139,7 +363,7 @@ __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, 
         }
         dst = cFU + (size_t)r * PU;
       }
-      if (!physical<D>(u, (double)ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
+      if (!physical<D>(u, ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
         dst[v] = u[v];
@@ -148,165 +372,25 @@ __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, 
       }
     }
     __syncthreads();
-    // ---- diagonal block, one column per local unit direction
-    for (int jj = 0; jj < nb; ++jj) {
-      const int w = jj / nm, i = jj % nm;
-      for (int t = threadIdx.x; t < nq + NF * nqf; t += blockDim.x) {
-        if (t < nq) {
-          int q = t;
-          using S = Dual<T>;
-          const T* pu = cU + (size_t)q * PU;
-          S u[M], g[M][D];
-          T p = mv.vphi[(size_t)q * nm + i];
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            u[v] = S(pu[v], v == w ? p : T(0));
-#pragma unroll
-            for (int kk = 0; kk < D; ++kk)
-              g[v][kk] = S(pu[M + v * D + kk], v == w ? mv.vdphi[((size_t)kk * nq + q) * nm + i] : T(0));
-          }
-          S F[M][D];
-          flux_total<D, S, T>(u, g, F, ph);
-          T wq = mv.vw[q];
-#pragma unroll
-          for (int v = 0; v < M; ++v)
-#pragma unroll
-            for (int kk = 0; kk < D; ++kk) bF[((size_t)q * M + v) * D + kk] = wq * F[v][kk].d;
-        } else {
-          int r = t - nq, s = r / nqf, q = r % nqf;
-          int k = s / 2, side = s % 2;
-          bool self = nbrs[s] == e;
-          T so = mv.fphi[((size_t)s * nqf + q) * nm + i];
-          T sgo[D], sgn[D];
-          T sn = self ? mv.fphi[((size_t)(s ^ 1) * nqf + q) * nm + i] : T(0);
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) {
-            sgo[kk] = mv.fdphi[(((size_t)s * D + kk) * nqf + q) * nm + i];
-            sgn[kk] = self ? mv.fdphi[(((size_t)(s ^ 1) * D + kk) * nqf + q) * nm + i] : T(0);
-          }
-          face_point_tangent<D, T>(cFU + ((size_t)(s * 2) * nqf + q) * PU,
-                                   cFU + ((size_t)(s * 2 + 1) * nqf + q) * PU, k, side, w, so, sgo,
-                                   sn, sgn, ph, bG + ((size_t)(s * 2) * nqf + q) * M,
-                                   bG + ((size_t)(s * 2 + 1) * nqf + q) * M,
-                                   bFp + ((size_t)s * nqf + q) * M, bDo + ((size_t)s * nqf + q) * M * D);
+    for (int w = 0; w < M; ++w) {
+      probe_sweep<D, T>(cx, TASK_VOL, -1, nq, w, nm, nm, De, nb);
+      probe_sweep<D, T>(cx, TASK_FACE_OWN, -1, NF * nqf, w, nm, nm, De, nb);
+      for (int s = 0; s < NF; ++s) {
+        if (nbrs[s] == e) {
+          probe_sweep<D, T>(cx, TASK_FACE_NBR, s, nqf, w, nm, nm, De, nb);
+        } else if (Oout != nullptr) {
+          probe_sweep<D, T>(cx, TASK_FACE_NBR, s, nqf, w, nmc, nmc, Oout + ((size_t)e * NF + s) * nbc * nbc, nbc);
         }
-      }
-      __syncthreads();
-      for (int t = threadIdx.x; t < NF * nqf; t += blockDim.x) {
-        int s = t / nqf, q = t % nqf, k = s / 2;
-        const T* PL = mv.lift + ((size_t)(2 * k + 1) * nqf + q) * nqf;
-        const T* PR = mv.lift + ((size_t)(2 * k) * nqf + q) * nqf;
-        T dl[M], dr[M];
-#pragma unroll
-        for (int v = 0; v < M; ++v) dl[v] = dr[v] = T(0);
-        for (int q2 = 0; q2 < nqf; ++q2) {
-          const T* gl = bG + ((size_t)(s * 2) * nqf + q2) * M;
-          const T* gr = bG + ((size_t)(s * 2 + 1) * nqf + q2) * M;
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            dl[v] += PL[q2] * gl[v];
-            dr[v] += PR[q2] * gr[v];
-          }
-        }
-        T* fo = bFp + ((size_t)s * nqf + q) * M;
-#pragma unroll
-        for (int v = 0; v < M; ++v) fo[v] += ph.eta * T(0.5) * (dl[v] + dr[v]);
-      }
-      __syncthreads();
-      for (int r = threadIdx.x; r < nb; r += blockDim.x) {
-        int v = r / nm, ip = r % nm;
-        T acc = T(0);
-        for (int q = 0; q < nq; ++q) {
-          const T* fq = bF + ((size_t)q * M + v) * D;
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) acc -= mv.vdphi[((size_t)kk * nq + q) * nm + ip] * fq[kk];
-        }
-#pragma unroll
-        for (int s = 0; s < NF; ++s) {
-          int k = s / 2;
-          T sg = (s % 2) ? T(1) : T(-1);
-          const T* fw = mv.fw + (size_t)k * nqf;
-          T a2 = T(0);
-          for (int q = 0; q < nqf; ++q) {
-            T x = sg * mv.fphi[((size_t)s * nqf + q) * nm + ip] * bFp[((size_t)s * nqf + q) * M + v];
-#pragma unroll
-            for (int kk = 0; kk < D; ++kk)
-              x -= mv.fdphi[(((size_t)s * D + kk) * nqf + q) * nm + ip] * bDo[(((size_t)s * nqf + q) * M + v) * D + kk];
-            a2 += fw[q] * x;
-          }
-          acc += a2;
-        }
-        if (r == jj) acc += sigma * mv.detJ;
-        Dout[((size_t)e * nb + r) * nb + jj] = acc;
-      }
-      __syncthreads();
-    }
-    // ---- neighbour blocks at coarse order (seed on the neighbour's trace)
-    if (Oout != nullptr) {
-      for (int jc = 0; jc < nbc; ++jc) {
-        const int w = jc / nmc, i = jc % nmc;
-        for (int t = threadIdx.x; t < NF * nqf; t += blockDim.x) {
-          int s = t / nqf, q = t % nqf, k = s / 2, side = s % 2;
-          T sgo[D], sgn[D];
-          T sn = mv.fphi[((size_t)(s ^ 1) * nqf + q) * nm + i];
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) {
-            sgo[kk] = T(0);
-            sgn[kk] = mv.fdphi[(((size_t)(s ^ 1) * D + kk) * nqf + q) * nm + i];
-          }
-          face_point_tangent<D, T>(cFU + ((size_t)(s * 2) * nqf + q) * PU,
-                                   cFU + ((size_t)(s * 2 + 1) * nqf + q) * PU, k, side, w, T(0), sgo,
-                                   sn, sgn, ph, bG + ((size_t)(s * 2) * nqf + q) * M,
-                                   bG + ((size_t)(s * 2 + 1) * nqf + q) * M,
-                                   bFp + ((size_t)s * nqf + q) * M, bDo + ((size_t)s * nqf + q) * M * D);
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < NF * nqf; t += blockDim.x) {
-          int s = t / nqf, q = t % nqf, k = s / 2;
-          const T* PL = mv.lift + ((size_t)(2 * k + 1) * nqf + q) * nqf;
-          const T* PR = mv.lift + ((size_t)(2 * k) * nqf + q) * nqf;
-          T dl[M], dr[M];
-#pragma unroll
-          for (int v = 0; v < M; ++v) dl[v] = dr[v] = T(0);
-          for (int q2 = 0; q2 < nqf; ++q2) {
-            const T* gl = bG + ((size_t)(s * 2) * nqf + q2) * M;
-            const T* gr = bG + ((size_t)(s * 2 + 1) * nqf + q2) * M;
-#pragma unroll
-            for (int v = 0; v < M; ++v) {
-              dl[v] += PL[q2] * gl[v];
-              dr[v] += PR[q2] * gr[v];
-            }
-          }
-          T* fo = bFp + ((size_t)s * nqf + q) * M;
-#pragma unroll
-          for (int v = 0; v < M; ++v) fo[v] += ph.eta * T(0.5) * (dl[v] + dr[v]);
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < NF * nbc; t += blockDim.x) {
-          int s = t / nbc, rc = t % nbc, v = rc / nmc, ip = rc % nmc, k = s / 2;
-          T sg = (s % 2) ? T(1) : T(-1);
-          const T* fw = mv.fw + (size_t)k * nqf;
-          T acc = T(0);
-          for (int q = 0; q < nqf; ++q) {
-            T x = sg * mv.fphi[((size_t)s * nqf + q) * nm + ip] * bFp[((size_t)s * nqf + q) * M + v];
-#pragma unroll
-            for (int kk = 0; kk < D; ++kk)
-              x -= mv.fdphi[(((size_t)s * D + kk) * nqf + q) * nm + ip] * bDo[(((size_t)s * nqf + q) * M + v) * D + kk];
-            acc += fw[q] * x;
-          }
-          if (nbrs[s] == e) acc = T(0);
-          Oout[(((size_t)e * NF + s) * nbc + rc) * nbc + jc] = acc;
-        }
-        __syncthreads();
       }
     }
+    __syncthreads();
   }
 }
 
 template <class T>
 size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem) {
   (void)nmc;
-  ProbeLayout<T> L(M.d, M.nb, M.nq, M.nqf);
+  ProbeLayout<T> L(M.d, M.nb, M.nm, M.nq, M.nqf);
   size_t bytes = L.total * sizeof(T);
   *fits_smem = bytes <= 220 * 1024;
   return L.total;

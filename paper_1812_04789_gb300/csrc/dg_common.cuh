@@ -313,15 +313,15 @@ __host__ __device__ __forceinline__ void face_point_k(int k, const S* uL, const 
 }
 
 // rho > 0 and p > 0 of a point state (primal values)
-template <int D, class S>
-__host__ __device__ __forceinline__ bool physical(const S* u, double gm1) {
+template <int D, class S, class T>
+__host__ __device__ __forceinline__ bool physical(const S* u, T gm1) {
   constexpr int M = D + 2;
-  double r = (double)val(u[0]);
-  double q = 0;
+  T r = val(u[0]);
+  T q = T(0);
 #pragma unroll
-  for (int j = 0; j < D; ++j) q += (double)val(u[1 + j]) * (double)val(u[1 + j]);
-  double p = gm1 * ((double)val(u[M - 1]) - 0.5 * q / r);
-  return r > 0 && p > 0;
+  for (int j = 0; j < D; ++j) q += val(u[1 + j]) * val(u[1 + j]);
+  T p = gm1 * (val(u[M - 1]) - T(0.5) * q / r);
+  return r > T(0) && p > T(0);
 }
 
 // ----------------------------------------------------------------- mesh view
@@ -341,6 +341,8 @@ struct MeshView {
   const T* fdphi;          // [2d][d][nqf][nm]
   const T* fw;             // [d][nqf]    face weights * |J_F|
   const T* lift;           // [2d][nqf][nqf] BR2 lifting operator (eq. re) incl. 1/(2|J|)
+  const T* liftT;          // [2d][2][nqf][nm] lifted test functions of local face f:
+                           //   sum_q fw(q) phi_i(q) P[q][q'], P = lift[2k+1] (c=0) or lift[2k] (c=1)
   T detJ;
 };
 

@@ -103,9 +103,9 @@ static cudaError_t upload(Mesh& M, const std::vector<double>& h, T** dst) {
 template <class T>
 static cudaError_t upload_tables(Mesh& M, Tables<T>& t, const std::vector<double>* tabs) {
   cudaError_t e;
-  T** dst[11] = {&t.vphiT, &t.vdphiT, &t.vphi, &t.vdphi, &t.vw, &t.fphiT,
-                 &t.fdphiT, &t.fphi, &t.fdphi, &t.fw, &t.lift};
-  for (int i = 0; i < 11; ++i)
+  T** dst[12] = {&t.vphiT, &t.vdphiT, &t.vphi, &t.vdphi, &t.vw, &t.fphiT,
+                 &t.fdphiT, &t.fphi, &t.fdphi, &t.fw, &t.lift, &t.liftT};
+  for (int i = 0; i < 12; ++i)
     if ((e = upload<T>(M, tabs[i], dst[i])) != cudaSuccess) return e;
   size_t ns = (size_t)M.E * M.d * 2 * M.nb;
   if ((e = cudaMalloc((void**)&t.slots, ns * sizeof(T))) != cudaSuccess) return e;
@@ -132,6 +132,7 @@ MeshView<double> Mesh::view<double>() const {
   v.vphiT = t64.vphiT; v.vdphiT = t64.vdphiT; v.vphi = t64.vphi; v.vdphi = t64.vdphi; v.vw = t64.vw;
   v.fphiT = t64.fphiT; v.fdphiT = t64.fdphiT; v.fphi = t64.fphi; v.fdphi = t64.fdphi; v.fw = t64.fw;
   v.lift = t64.lift;
+  v.liftT = t64.liftT;
   v.detJ = detJ;
   return v;
 }
@@ -144,6 +145,7 @@ MeshView<float> Mesh::view<float>() const {
   v.vphiT = t32.vphiT; v.vdphiT = t32.vdphiT; v.vphi = t32.vphi; v.vdphi = t32.vdphi; v.vw = t32.vw;
   v.fphiT = t32.fphiT; v.fdphiT = t32.fdphiT; v.fphi = t32.fphi; v.fdphi = t32.fdphi; v.fw = t32.fw;
   v.lift = t32.lift;
+  v.liftT = t32.liftT;
   v.detJ = (float)detJ;
   return v;
 }
@@ -203,10 +205,11 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
   auto dL1 = [&](int a, int deg) { return dL[(size_t)a * (p + 1) + deg]; };
 
   const int nq = M.nq, nqf = M.nqf, nm = M.nm;
-  std::vector<double> tabs[11];
+  std::vector<double> tabs[12];
   std::vector<double>&vphiT = tabs[0], &vdphiT = tabs[1], &vphi = tabs[2], &vdphi = tabs[3], &vw = tabs[4];
   std::vector<double>&fphiT = tabs[5], &fdphiT = tabs[6], &fphi = tabs[7], &fdphi = tabs[8], &fw = tabs[9];
   std::vector<double>& lift = tabs[10];
+  std::vector<double>& liftT = tabs[11];
   vphiT.assign((size_t)nm * nq, 0);
   vdphiT.assign((size_t)d * nm * nq, 0);
   vphi.assign((size_t)nq * nm, 0);
@@ -291,6 +294,25 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
           s += fphi[((size_t)f * nqf + q) * nm + i] * fphi[((size_t)f * nqf + q2) * nm + i];
         lift[((size_t)f * nqf + q) * nqf + q2] = cl * s * wraw[q2];
       }
+  }
+  // lifted test functions: the BR2 term sum_q fw(q) phi_i(q) {delta}(q) is linear
+  // in the lifted tensors, so it equals sum_q' liftT[f][c][q'][i] G_c(q') with
+  // liftT[f][c][q'][i] = sum_q fw(q) phi^f_i(q) P_c[q][q'], P_0 = lift of the face's
+  // +k side (2k+1), P_1 = lift of its -k side (2k)
+  liftT.assign((size_t)nf * 2 * nqf * nm, 0);
+  for (int f = 0; f < nf; ++f) {
+    int k = f / 2;
+    for (int c = 0; c < 2; ++c) {
+      int pf = c == 0 ? 2 * k + 1 : 2 * k;
+      for (int q2 = 0; q2 < nqf; ++q2)
+        for (int i = 0; i < nm; ++i) {
+          double s = 0;
+          for (int q = 0; q < nqf; ++q)
+            s += fw[(size_t)k * nqf + q] * fphi[((size_t)f * nqf + q) * nm + i] *
+                 lift[((size_t)pf * nqf + q) * nqf + q2];
+          liftT[(((size_t)f * 2 + c) * nqf + q2) * nm + i] = s;
+        }
+    }
   }
   // neighbours
   std::vector<int> nbr((size_t)M.E * d * 2);

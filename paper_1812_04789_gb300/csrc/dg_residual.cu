@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) face_kernel(MeshView<T> mv, Phys<T> ph,
         }
       }
     }
-    if (!physical<D>(uL, (double)ph.gm1) || !physical<D>(uR, (double)ph.gm1))
+    if (!physical<D>(uL, ph.gm1) || !physical<D>(uR, ph.gm1))
       atomicOr(status, ST_NONPHYSICAL);
     S fp[M], GLn[M], GRn[M], DL[M][D], DR[M][D];
     face_point_k<D, S, T>(k, uL, gL, uR, gR, ph, fp, GLn, GRn, DL, DR);
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) volume_kernel(MeshView<T> mv, Phys<T> ph,
         for (int kk = 0; kk < D; ++kk) g[v][kk] = g[v][kk] + a * dp[kk];
       }
     }
-    if (!physical<D>(u, (double)ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
+    if (!physical<D>(u, ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
     S F[M][D];
     flux_total<D, S, T>(u, g, F, ph);
     T wq = mv.vw[q];
