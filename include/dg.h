@@ -212,6 +212,55 @@ dg_status dg_axpy(dg_mesh mesh, double alpha, const double* x, double* y, void* 
  * (host-side counter; for launch accounting in benchmarks). */
 dg_status dg_launch_count(unsigned long long* count);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop over implicit steps (no counterpart in the paper: it serves
+ * many independent cases of the step above on one GPU).  A request is one BDF2
+ * step of one case, solved as in dg_fgmres_step with the p-multigrid
+ * preconditioner refreshed at W^n.  Requests are admitted as device memory
+ * frees up: each runs in a resident slot (mesh + p-multigrid handles + Krylov
+ * workspace + its own stream) that stays alive after completion and is reused
+ * by later requests of the same shape (mesh descriptor, physics, options);
+ * idle slots are evicted least-recently-used to stay within the byte budget.
+ * `workers` requests run at a time on separate streams, so their kernels
+ * overlap on the device; new requests are admitted while others run
+ * (continuous batching).  The result of a request does not depend on what else
+ * is in flight (deterministic kernels, private buffers). */
+typedef struct dg_server_s* dg_server;
+
+typedef struct {
+  long long id;
+  int status;            /* dg_status of the request */
+  double latency_ms;     /* submit to completion, host clock */
+  double queue_ms;       /* submit to start */
+  int fgmres_iters;      /* FGMRES iterations over the step's Newton iterations */
+  long long ndofs;
+} dg_server_result;
+
+/* Start `workers` (1..64) worker threads on the current device with a device
+ * memory budget in bytes.  DG_ERR_INVALID on bad arguments. */
+dg_status dg_server_create(size_t budget_bytes, int workers, dg_server* out);
+
+/* Queue one request.  Wn, Wnm1 (inputs) and Wout (the step's result W^{n+1})
+ * are host arrays of E*m*n_m doubles that must stay valid until the request's
+ * completion has been returned by dg_server_poll.  A request whose estimated
+ * footprint exceeds the whole budget completes with DG_ERR_OOM. */
+dg_status dg_server_submit(dg_server server, long long id, const dg_mesh_desc* desc, const dg_physics* phys,
+                           const dg_pmg_opts* opts, const double* Wn, const double* Wnm1, double dt, int newton,
+                           double rtol, double* Wout);
+
+/* Wait until at least min_done completions are pending (timeout_ms < 0: no
+ * limit), then move up to cap of them (oldest first) into out; *n_out = count.
+ * DG_ERR_TIMEOUT if the wait ran out first (whatever was ready is returned). */
+dg_status dg_server_poll(dg_server server, int min_done, int timeout_ms, dg_server_result* out, int cap,
+                         int* n_out);
+
+/* Device bytes held by resident slots, slot count, requests submitted/completed. */
+dg_status dg_server_stats(dg_server server, size_t* used_bytes, int* resident_slots, long long* submitted,
+                          long long* completed);
+
+/* Stop the workers after their current requests, free every slot. */
+dg_status dg_server_destroy(dg_server server);
+
 /* Synchronise `stream`, return the mesh's device status word (DG_OK if no
  * device-side problem was recorded since the last call) and clear it. */
 dg_status dg_status_sync(dg_mesh mesh, void* stream);

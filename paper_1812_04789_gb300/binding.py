@@ -271,3 +271,95 @@ class PMG:
             raise DGError("dg_fgmres_step", code)
         return out
 
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("latency_ms", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("fgmres_iters", ctypes.c_int), ("ndofs", ctypes.c_longlong)]
+
+
+_SERVER_SIGS = {
+    "dg_server_create": [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(P)],
+    "dg_server_submit": [P, ctypes.c_longlong, ctypes.POINTER(MeshDesc), ctypes.POINTER(PhysicsDesc),
+                         ctypes.POINTER(PmgOpts), P, P, ctypes.c_double, ctypes.c_int, ctypes.c_double, P],
+    "dg_server_poll": [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ServerResult), ctypes.c_int,
+                       ctypes.POINTER(ctypes.c_int)],
+    "dg_server_stats": [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
+                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)],
+    "dg_server_destroy": [P],
+}
+EXPORTED += list(_SERVER_SIGS)
+
+
+def _server_lib():
+    lib = load()
+    for name, args in _SERVER_SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    return lib
+
+
+def mesh_desc_struct(desc):
+    d = MeshDesc()
+    d.dim = desc["dim"]
+    n = list(desc["n"]) + [1] * (3 - len(desc["n"]))
+    lo = list(desc["lo"]) + [0.0] * (3 - len(desc["lo"]))
+    hi = list(desc["hi"]) + [1.0] * (3 - len(desc["hi"]))
+    for k in range(3):
+        d.n[k], d.lo[k], d.hi[k] = int(n[k]), float(lo[k]), float(hi[k])
+    d.p, d.nq1d = int(desc["p"]), int(desc.get("nq1d", 0))
+    return d
+
+
+def physics_struct(phys):
+    return PhysicsDesc(phys["gamma"], phys["Pr"], phys["mu"], phys["Rgas"], phys.get("eta", 0.0) or 0.0,
+                       phys["roe_delta"])
+
+
+class Server:
+    """Continuous-batching request loop over implicit steps (dg_server_*).
+    Host arrays passed to submit() are kept referenced until their completion
+    has been polled."""
+
+    def __init__(self, budget_bytes, workers=4):
+        self.lib = _server_lib()
+        h = P()
+        _check("dg_server_create", self.lib.dg_server_create(int(budget_bytes), int(workers), ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, rid, desc, phys, opts, Wn, Wnm1, dt, Wout, newton=2, rtol=1e-5):
+        import numpy as np
+        for a in (Wn, Wnm1, Wout):
+            assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+        d, p = mesh_desc_struct(desc), physics_struct(phys)
+        self._keep[rid] = (Wn, Wnm1, Wout, d, p, opts)
+        _check("dg_server_submit", self.lib.dg_server_submit(
+            self.h, int(rid), ctypes.byref(d), ctypes.byref(p), ctypes.byref(opts), Wn.ctypes.data,
+            Wnm1.ctypes.data, float(dt), int(newton), float(rtol), Wout.ctypes.data))
+
+    def poll(self, min_done=1, timeout_ms=-1, cap=256):
+        buf = (ServerResult * cap)()
+        n = ctypes.c_int()
+        self.lib.dg_server_poll(self.h, int(min_done), int(timeout_ms), buf, cap, ctypes.byref(n))
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            out.append(dict(id=r.id, status=r.status, latency_ms=r.latency_ms, queue_ms=r.queue_ms,
+                            fgmres_iters=r.fgmres_iters, ndofs=r.ndofs))
+            self._keep.pop(r.id, None)
+        return out
+
+    def stats(self):
+        u, s, a, b = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check("dg_server_stats", self.lib.dg_server_stats(self.h, ctypes.byref(u), ctypes.byref(s),
+                                                           ctypes.byref(a), ctypes.byref(b)))
+        return dict(used_bytes=u.value, resident_slots=s.value, submitted=a.value, completed=b.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dg_server_destroy(self.h)
+            self.h = None
+
+    __del__ = close

@@ -220,3 +220,34 @@ def batch_cases(count=64, seed=SEED):
         cfg["amp"] = float(rng.uniform(0.95, 1.05))
         out.append(cfg)
     return out
+
+
+def serving_requests(count=32, seed=1812, max_dofs=None):
+    """Request mix of the serving workload: 2-D vortex quads 32^2-256^2 and 3-D
+    TGV hexes 8^3-32^3 with equal probability, p ~ U{1..6}, FP64 or mixed with
+    probability 1/2, each one implicit BDF2 step.  max_dofs (optional) bounds
+    the sample: a draw whose DOFs exceed it is redrawn (a bounded sample of the
+    same distribution, for runs that must finish in minutes)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        if rng.uniform() < 0.5:
+            n = int(rng.integers(32, 257))
+            p = int(rng.integers(1, 7))
+            cfg = make_config("vortex", 2, (n, n), p, M=0.5, Re=1000.0, dt_conv=0.05)
+        else:
+            n = int(rng.integers(8, 33))
+            p = int(rng.integers(1, 7))
+            cfg = make_config("tgv", 3, (n, n, n), p, M=0.1, Re=1600.0, dt_conv=0.01)
+        levels = [p]
+        for q in (2, 1, 0):
+            if q < levels[-1]:
+                levels.append(q)
+        cfg["p_levels"] = tuple(levels)
+        cfg["mixed"] = bool(rng.uniform() < 0.5)
+        dofs = n_elements(cfg) * (cfg["dim"] + 2) * n_modes(p, cfg["dim"])
+        if max_dofs is not None and dofs > max_dofs:
+            continue
+        cfg["dofs"] = dofs
+        out.append(cfg)
+    return out
