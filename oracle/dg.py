@@ -181,15 +181,17 @@ def mass_apply(mesh, v):
     return mesh.detJ * v
 
 
-def jvp(mesh, ph, W, v, sigma, h=1e-30):
+def jvp(mesh, ph, W, v, sigma, h=1e-30, elems=None):
     """Exact K v = sigma M v + dR/dW(W) v (Sec. 5.1, eq. ODEDG), with the
     directional derivative taken by the complex step Im R(W + i h v)/h
     (Squire & Trapp 1998): no subtractive cancellation, so it equals the exact
-    derivative up to rounding.  sigma is 1/(a_ii dt) (ESDIRK) or 3/(2 dt) (BDF2)."""
+    derivative up to rounding.  sigma is 1/(a_ii dt) (ESDIRK) or 3/(2 dt) (BDF2).
+    elems (optional): return only those elements' rows."""
     scale = max(1.0, float(np.max(np.abs(v)))) if v.size else 1.0
     hh = h / scale
-    Rc = residual(mesh, ph, W.astype(np.complex128) + 1j * hh * v)
-    return sigma * mass_apply(mesh, v) + Rc.imag / hh
+    Rc = residual(mesh, ph, W.astype(np.complex128) + 1j * hh * v, elems=elems)
+    vt = v if elems is None else v[np.asarray(elems, dtype=np.int64)]
+    return sigma * mass_apply(mesh, vt) + Rc.imag / hh
 
 
 def jvp_fd(mesh, ph, W, RW, v, sigma, eps=1e-7, variant="printed"):
