@@ -129,8 +129,8 @@ dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma,
 
 /* p-multigrid options (Sec. 6; Table MGSettings).  p_level[0] must equal the
  * mesh degree and the levels must decrease strictly.  Every smoother is GMRES
- * right-preconditioned by element block Jacobi; nu_pre/nu_post per level
- * (ignored on the coarsest), nu_coarse on the coarsest level. */
+ * right-preconditioned by element block Jacobi; nu_pre/nu_post (0..64) per level
+ * (ignored on the coarsest), nu_coarse (1..64) on the coarsest level. */
 typedef struct {
   int n_levels;
   int p_level[8];

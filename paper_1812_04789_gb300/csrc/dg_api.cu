@@ -314,9 +314,9 @@ static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
   if (o->p_level[0] != mesh->m.p) return DG_ERR_INVALID;
   for (int l = 1; l < o->n_levels; ++l)
     if (o->p_level[l] < 0 || o->p_level[l] >= o->p_level[l - 1]) return DG_ERR_INVALID;
-  if (o->nu_coarse < 1 || o->nu_coarse > 256) return DG_ERR_INVALID;
+  if (o->nu_coarse < 1 || o->nu_coarse > 64) return DG_ERR_INVALID;
   for (int l = 0; l + 1 < o->n_levels; ++l)
-    if (o->nu_pre[l] < 0 || o->nu_post[l] < 0 || o->nu_pre[l] > 256 || o->nu_post[l] > 256) return DG_ERR_INVALID;
+    if (o->nu_pre[l] < 0 || o->nu_post[l] < 0 || o->nu_pre[l] > 64 || o->nu_post[l] > 64) return DG_ERR_INVALID;
   return DG_OK;
 }
 

@@ -589,8 +589,20 @@ template cudaError_t launch_truncate_blocks<float>(const float*, int, float*, in
 
 // ---------------------------------------------------------------- block apply / BSR
 // One CTA per element: the element's input (and neighbours' for BSR) staged in
-// shared memory, one warp per block row with the lanes striding the columns
-// (coalesced row reads), fixed butterfly reduction.
+// shared memory; each warp takes two block rows at a time, the lanes striding
+// the columns with an unrolled loop (coalesced row reads, several loads in
+// flight per lane, conflict-free shared reads); fixed butterfly reductions.
+template <class T>
+__device__ __forceinline__ void row_dot2(const T* __restrict__ A0, const T* __restrict__ A1, const T* xs, int n,
+                                         int lane, T& s0, T& s1) {
+#pragma unroll 4
+  for (int c = lane; c < n; c += 32) {
+    const T xv = xs[c];
+    s0 += __ldg(A0 + c) * xv;
+    s1 += __ldg(A1 + c) * xv;
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, const T* __restrict__ O,
                                                   const int* __restrict__ nbr, int nf, const T* __restrict__ x,
@@ -606,20 +618,25 @@ __global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, cons
       xs[t] = x[(size_t)el * nb + j];
     }
     __syncthreads();
-    for (int r = warp; r < nb; r += nw) {
-      T acc = T(0);
-      const T* Ar = Dm + ((size_t)e * nb + r) * nb;
-      for (int c = lane; c < nb; c += 32) acc += Ar[c] * xs[c];
+    for (int r0 = 2 * warp; r0 < nb; r0 += 2 * nw) {
+      const int r1 = min(r0 + 1, nb - 1);     // an odd last row is computed twice, stored once
+      T s0 = T(0), s1 = T(0);
+      row_dot2<T>(Dm + ((size_t)e * nb + r0) * nb, Dm + ((size_t)e * nb + r1) * nb, xs, nb, lane, s0, s1);
       if (O) {
         for (int s = 0; s < nf; ++s) {
-          const T* Orow = O + (((size_t)e * nf + s) * nb + r) * nb;
-          const T* xn = xs + (size_t)(1 + s) * nb;
-          for (int c = lane; c < nb; c += 32) acc += Orow[c] * xn[c];
+          const T* Ob = O + ((size_t)e * nf + s) * nb * nb;
+          row_dot2<T>(Ob + (size_t)r0 * nb, Ob + (size_t)r1 * nb, xs + (size_t)(1 + s) * nb, nb, lane, s0, s1);
         }
       }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) y[(size_t)e * nb + r] = acc;
+      for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+      }
+      if (lane == 0) {
+        y[(size_t)e * nb + r0] = s0;
+        if (r1 != r0) y[(size_t)e * nb + r1] = s1;
+      }
     }
     __syncthreads();
   }
