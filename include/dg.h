@@ -270,11 +270,15 @@ dg_status dg_pmg_bytes(dg_pmg pmg, size_t* block_bytes, size_t* vector_bytes);
 
 #define DG_BLOCKS_DIAG_INV 0   /* inverse diagonal blocks, E * nb * nb */
 #define DG_BLOCKS_NEIGHBOUR 1  /* neighbour blocks, E * 2d * nb * nb, [e][2k+side] */
+#define DG_BLOCKS_DIAG 2       /* diagonal blocks before inversion, E * nb * nb */
 
 /* Copy the blocks of level `level` into a caller device buffer (entries of the
  * handle's precision: FP64, or FP32 in mixed mode; nb = m * n_m(p_level[level]);
  * row-major [v*n_m + i][w*n_m + j]), for testing and inspection.  Neighbour
- * blocks exist for levels >= 1 (side 0 = the xi_k = -1 face).  Synchronous.
+ * blocks exist for levels >= 1 (side 0 = the xi_k = -1 face).  DG_BLOCKS_DIAG
+ * (Sec. 5.1 eq. ODEDG, d R_e / d W_e + sigma |J| I): level 0 is recomputed by
+ * the fine-level probe at the handle's state and shift, written straight into
+ * `out`; coarser levels are the inherited (truncated) blocks.  Synchronous.
  * DG_ERR_INVALID if the level or kind does not exist or out_bytes is short. */
 dg_status dg_pmg_export_blocks(dg_pmg pmg, int level, int which, void* out, size_t out_bytes,
                                void* stream);

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID", 2: "DG_ERR_OOM", 3: "DG_ERR_CUD
 JVP_EXACT, JVP_FD, JVP_FD_SCALED = 0, 1, 2
 CYCLE_FMG, CYCLE_V, CYCLE_BJ = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
-BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR = 0, 1
+BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR, BLOCKS_DIAG = 0, 1, 2
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",

@@ -377,6 +377,8 @@ extern "C" dg_status dg_pmg_setup(dg_mesh mesh, const double* W, double sigma, c
     if (cudaMemcpyAsync(&hs, mesh->m.status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       s = DG_ERR_CUDA;
+    else if (hs & ST_TIMEOUT)
+      s = DG_ERR_TIMEOUT;
     else if (hs & ST_SINGULAR)
       s = DG_ERR_BREAKDOWN;
     else if (hs & ST_NONPHYSICAL)
@@ -455,6 +457,23 @@ extern "C" dg_status dg_pmg_export_blocks(dg_pmg h, int level, int which, void* 
     if (level < 1) return DG_ERR_INVALID;
     src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].O : (const void*)h->mg32.lv[level].O;
     cnt = (size_t)M.E * 2 * M.d * nb * nb;
+  } else if (which == DG_BLOCKS_DIAG) {
+    cnt = (size_t)M.E * nb * nb;
+    if (out_bytes < cnt * es) return DG_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (level == 0) {   // the fine-level probe again, at the stored state and shift
+      if (h->precision == DG_PREC_FP64)
+        CK(launch_probe_blocks<double>(M, h->mg64.W, h->sigma, (double*)out, nullptr, 0, h->mg64.scratch,
+                                       h->mg64.scratch_elems, st));
+      else
+        CK(launch_probe_blocks<float>(M, h->mg32.W, (float)h->sigma, (float*)out, nullptr, 0, h->mg32.scratch,
+                                      h->mg32.scratch_elems, st));
+    } else {
+      src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].Dop : (const void*)h->mg32.lv[level].Dop;
+      CK(cudaMemcpyAsync(out, src, cnt * es, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return DG_OK;
   } else {
     return DG_ERR_INVALID;
   }
@@ -544,7 +563,8 @@ extern "C" dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, c
   if (s == DG_OK) {
     int hs = 0;
     cudaMemcpy(&hs, M.status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (hs & ST_NONPHYSICAL) s = DG_ERR_NONPHYSICAL;
+    if (hs & ST_TIMEOUT) s = DG_ERR_TIMEOUT;
+    else if (hs & ST_NONPHYSICAL) s = DG_ERR_NONPHYSICAL;
   }
   if (stats) {
     stats->iters = iters;

@@ -19,9 +19,11 @@
 // with one element makes the element its own neighbour: the neighbour-side
 // seed of such a face then adds to the diagonal block.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "dg_internal.h"
+#include "dg_probe.cuh"
 
 namespace dgk {
 
@@ -51,42 +53,6 @@ struct ProbeLayout {
     total = o;
   }
 };
-
-// Tangent of the face-point outputs for a unit seed: so/sgo on the own trace,
-// sn/sgn on the neighbour's.  Outputs: numerical flux fp[v], lifting integrands
-// GL[v], GR[v] of the face's +k / -k sides, and the element's own dual tensor.
-template <int D, class T>
-__device__ __forceinline__ void face_point_tangent(const T* pu_own, const T* pu_nb, int k, int side,
-                                                   int w, T so, const T* sgo, T sn, const T* sgn,
-                                                   const Phys<T>& ph, T* bGL, T* bGR, T* bFp,
-                                                   T* bDo) {
-  using S = Dual<T>;
-  constexpr int M = D + 2;
-  S uo[M], un[M], go[M][D], gn[M][D];
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    uo[v] = S(pu_own[v], v == w ? so : T(0));
-    un[v] = S(pu_nb[v], v == w ? sn : T(0));
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) {
-      go[v][kk] = S(pu_own[M + v * D + kk], v == w ? sgo[kk] : T(0));
-      gn[v][kk] = S(pu_nb[M + v * D + kk], v == w ? sgn[kk] : T(0));
-    }
-  }
-  S fp[M], GLn[M], GRn[M], DL[M][D], DR[M][D];
-  if (side)
-    face_point_k<D, S, T>(k, uo, go, un, gn, ph, fp, GLn, GRn, DL, DR);
-  else
-    face_point_k<D, S, T>(k, un, gn, uo, go, ph, fp, GLn, GRn, DL, DR);
-#pragma unroll
-  for (int v = 0; v < M; ++v) {
-    bFp[v] = tan_part(fp[v]);
-    bGL[v] = tan_part(GLn[v]);
-    bGR[v] = tan_part(GRn[v]);
-#pragma unroll
-    for (int kk = 0; kk < D; ++kk) bDo[v * D + kk] = tan_part(side ? DL[v][kk] : DR[v][kk]);
-  }
-}
 
 enum ProbeTask : int { TASK_VOL = 0, TASK_FACE_OWN = 1, TASK_FACE_NBR = 2 };
 
@@ -289,7 +255,8 @@ __device__ __forceinline__ void probe_sweep(const ProbeCtx<T>& cx, int task, int
 template <int D, class T>
 __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, const T* __restrict__ W,
                                                     T sigma, T* __restrict__ Dout, T* __restrict__ Oout,
-                                                    int nmc, T* gscratch, int use_smem, int* status) {
+                                                    int nmc, T* gscratch, int use_smem, int nbr_only,
+                                                    int* status) {
   constexpr int M = D + 2, NF = 2 * D, PU = M * (1 + D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = mv.nb, nm = mv.nm, nq = mv.nq, nqf = mv.nqf, E = mv.E;
@@ -313,68 +280,16 @@ __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, 
 #pragma unroll
     for (int s = 0; s < NF; ++s) nbrs[s] = mv.nbr[e * NF + s];
     T* De = Dout + (size_t)e * nb * nb;
-    for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) De[t] = (t / nb == t % nb) ? sigma * mv.detJ : T(0);
+    if (!nbr_only)
+      for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) De[t] = (t / nb == t % nb) ? sigma * mv.detJ : T(0);
     if (Oout)
       for (int t = threadIdx.x; t < NF * nbc * nbc; t += blockDim.x) Oout[(size_t)e * NF * nbc * nbc + t] = T(0);
-    // ---- stage W of the element and its neighbours (face order s = 2k + side)
-    for (int t = threadIdx.x; t < (1 + NF) * nb; t += blockDim.x) {
-      int who = t / nb, j = t % nb;
-      int el = who == 0 ? e : nbrs[who - 1];
-      cW[t] = W[(size_t)el * nb + j];
-    }
-    __syncthreads();
-    // ---- primal traces: volume points and both sides of every face
-    for (int t = threadIdx.x; t < nq + NF * 2 * nqf; t += blockDim.x) {
-      T u[M], g[M][D];
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        u[v] = T(0);
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) g[v][kk] = T(0);
-      }
-      T* dst;
-      if (t < nq) {
-        int q = t;
-        for (int i = 0; i < nm; ++i) {
-          T p = mv.vphiT[(size_t)i * nq + q];
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            T a = cW[v * nm + i];
-            u[v] += a * p;
-#pragma unroll
-            for (int kk = 0; kk < D; ++kk) g[v][kk] += a * mv.vdphiT[((size_t)kk * nm + i) * nq + q];
-          }
-        }
-        dst = cU + (size_t)q * PU;
-      } else {
-        int r = t - nq, s = r / (2 * nqf), who = (r / nqf) % 2, q = r % nqf;
-        int lf = who == 0 ? s : (s ^ 1);               // own face s, neighbour's face s^1
-        const T* ws = cW + (size_t)(who == 0 ? 0 : 1 + s) * nb;
-        for (int i = 0; i < nm; ++i) {
-          T p = mv.fphiT[((size_t)lf * nm + i) * nqf + q];
-#pragma unroll
-          for (int v = 0; v < M; ++v) {
-            T a = ws[v * nm + i];
-            u[v] += a * p;
-#pragma unroll
-            for (int kk = 0; kk < D; ++kk)
-              g[v][kk] += a * mv.fdphiT[(((size_t)lf * D + kk) * nm + i) * nqf + q];
-          }
-        }
-        dst = cFU + (size_t)r * PU;
-      }
-      if (!physical<D>(u, ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        dst[v] = u[v];
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) dst[M + v * D + kk] = g[v][kk];
-      }
-    }
-    __syncthreads();
+    probe_stage_primal<D, T>(mv, ph, W, e, nbrs, cW, cU, cFU, !nbr_only, status);
     for (int w = 0; w < M; ++w) {
-      probe_sweep<D, T>(cx, TASK_VOL, -1, nq, w, nm, nm, De, nb);
-      probe_sweep<D, T>(cx, TASK_FACE_OWN, -1, NF * nqf, w, nm, nm, De, nb);
+      if (!nbr_only) {
+        probe_sweep<D, T>(cx, TASK_VOL, -1, nq, w, nm, nm, De, nb);
+        probe_sweep<D, T>(cx, TASK_FACE_OWN, -1, NF * nqf, w, nm, nm, De, nb);
+      }
       for (int s = 0; s < NF; ++s) {
         if (nbrs[s] == e) {
           probe_sweep<D, T>(cx, TASK_FACE_NBR, s, nqf, w, nm, nm, De, nb);
@@ -410,7 +325,7 @@ int probe_grid_global() { return 2 * num_sms(); }
 
 template <int D, class T>
 static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, T* Oout, int nmc, T* scratch,
-                             size_t scratch_elems, cudaStream_t st) {
+                             size_t scratch_elems, bool nbr_only, cudaStream_t st) {
   bool fits;
   size_t tot = probe_scratch_elems<T>(Ms, nmc, &fits);
   int grid;
@@ -426,15 +341,33 @@ static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, T* Oo
   }
   note_launch();
   probe_kernel<D, T><<<grid, 256, smem, st>>>(Ms.view<T>(), Ms.phys_t<T>(), W, sigma, Dout, Oout, nmc,
-                                             scratch, fits ? 1 : 0, Ms.status);
+                                             scratch, fits ? 1 : 0, nbr_only ? 1 : 0, Ms.status);
   return cudaGetLastError();
+}
+
+// FP32 blocks go through the tensor-core kernel when the mesh has a plan for
+// it (DG_PROBE_SIMT=1 in the environment selects the SIMT kernel instead); the
+// SIMT kernel then adds only the neighbour-seeded terms: the coarse neighbour
+// blocks, and the faces of a direction with one element (own neighbour).
+static bool use_tc(const Mesh& M) {
+  const char* e = getenv("DG_PROBE_SIMT");
+  return M.tc.ok && M.tc_test && M.tc_trial && !(e && e[0] == '1');
 }
 
 template <class T>
 cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, T* O, int nmc, T* scratch,
                                 size_t scratch_elems, cudaStream_t st) {
-  if (M.d == 2) return run_probe<2, T>(M, W, sigma, D, O, nmc, scratch, scratch_elems, st);
-  return run_probe<3, T>(M, W, sigma, D, O, nmc, scratch, scratch_elems, st);
+  bool nbr_only = false;
+  if (std::is_same<T, float>::value && use_tc(M)) {
+    cudaError_t e = launch_probe_tc(M, (const float*)W, (float)sigma, (float*)D, st);
+    if (e != cudaSuccess) return e;
+    bool self = false;
+    for (int k = 0; k < M.d; ++k) self = self || M.desc.n[k] == 1;
+    if (O == nullptr && !self) return cudaSuccess;
+    nbr_only = true;
+  }
+  if (M.d == 2) return run_probe<2, T>(M, W, sigma, D, O, nmc, scratch, scratch_elems, nbr_only, st);
+  return run_probe<3, T>(M, W, sigma, D, O, nmc, scratch, scratch_elems, nbr_only, st);
 }
 template cudaError_t launch_probe_blocks<double>(const Mesh&, const double*, double, double*, double*, int,
                                                  double*, size_t, cudaStream_t);

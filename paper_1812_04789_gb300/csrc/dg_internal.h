@@ -11,7 +11,7 @@
 
 namespace dgk {
 
-enum : int { ST_NONPHYSICAL = 1, ST_SINGULAR = 2, ST_NONFINITE = 4 };
+enum : int { ST_NONPHYSICAL = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
 
 // host-side count of kernel launches (dg_launch_count)
 unsigned long long& launch_counter();
@@ -29,6 +29,18 @@ struct Tables {
   T* fd_r = nullptr;         // finite-difference JVP scratch: R(W + h v)
 };
 
+// Plan of the tensor-core block probe (FP32 blocks): seed variables are taken
+// in groups of G whose accumulators, rows (w, v, i') x npad columns in
+// 128-row tiles, fit the 512 TMEM columns; points are taken jq at a time,
+// two points (8 K values: point x {value, d gradients, pad}) per MMA K step.
+// Byte offsets of the shared-memory regions; ok = 0 when no plan fits.
+struct TcPlan {
+  int ok = 0;
+  int G = 0, ngroups = 0, tiles = 0, npad = 0, nmp = 0, jq = 0, npv = 0, nks = 0, tmem_cols = 0;
+  int oA = 0, oB = 0, oJ = 0, oT = 0, oW = 0, oU = 0, oFU = 0, smem = 0;
+};
+TcPlan tc_plan(int d, int nm, int nq, int nqf, int smem_max);
+
 struct Mesh {
   dg_mesh_desc desc;
   dg_physics phys;
@@ -37,6 +49,9 @@ struct Mesh {
   int* nbr = nullptr;        // device [E][d][2]
   Tables<double> t64;
   Tables<float> t32;
+  TcPlan tc;                 // tensor-core probe plan and its element-independent tables:
+  float* tc_test = nullptr;  //   test rows [point][kind][nmp] (weights, signs, lifting folded in)
+  float* tc_trial = nullptr; //   trial operand per K step [nks][hi, lo][npad x 8] in MMA layout
   int* status = nullptr;     // device status word
   double* scal = nullptr;    // device scalars for the FD JVP (norms, h)
   double* partials = nullptr;// reduction partials for the FD JVP norms
@@ -65,6 +80,12 @@ cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, T* O, 
                                 T* scratch, size_t scratch_elems, cudaStream_t st);
 template <class T>
 size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem);
+
+// Tensor-core probe of the FP32 diagonal blocks: D[e] = dR_e/dW_e (volume and
+// own-face seeds) + sigma |J| I, written in full.  Neighbour-seeded terms are
+// the SIMT kernel's.  build_tc_tables fills the mesh's tables (M.tc.ok).
+cudaError_t launch_probe_tc(const Mesh& M, const float* W, float sigma, float* D, cudaStream_t st);
+cudaError_t build_tc_tables(Mesh& M);
 
 // Batched in-place inverse of nblk blocks of size nb (Gauss-Jordan, partial pivoting).
 template <class T>

@@ -347,6 +347,8 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
   M.allocs.push_back(M.scal);
   if (cudaMalloc((void**)&M.partials, 2 * 1024 * sizeof(double)) != cudaSuccess) return DG_ERR_OOM;
   M.allocs.push_back(M.partials);
+  if ((err = build_tc_tables(M)) != cudaSuccess)
+    return err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
   return DG_OK;
 }
 
@@ -411,6 +413,7 @@ extern "C" dg_status dg_status_sync(dg_mesh mesh, void* stream) {
     return DG_ERR_CUDA;
   if (cudaMemsetAsync(mesh->m.status, 0, sizeof(int), st) != cudaSuccess) return DG_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return DG_ERR_CUDA;
+  if (h & ST_TIMEOUT) return DG_ERR_TIMEOUT;
   if (h & ST_NONPHYSICAL) return DG_ERR_NONPHYSICAL;
   if (h & (ST_SINGULAR | ST_NONFINITE)) return DG_ERR_BREAKDOWN;
   return DG_OK;
