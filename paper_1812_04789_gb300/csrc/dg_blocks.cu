@@ -374,125 +374,6 @@ template cudaError_t launch_probe_blocks<double>(const Mesh&, const double*, dou
 template cudaError_t launch_probe_blocks<float>(const Mesh&, const float*, float, float*, float*, int, float*,
                                                 size_t, cudaStream_t);
 
-// ---------------------------------------------------------------- block inverse
-// In-place Gauss-Jordan inversion with partial (row) pivoting: the largest
-// |entry| of the pivot column, the lowest row index on ties; the row swaps
-// are undone on the columns of the inverse at the end.  A zero pivot marks the
-// status word and leaves the block unusable.
-template <class T>
-__global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ blocks, int nb, long nblk,
-                                                            int use_smem, int* status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // byte layout: rv[blockDim] doubles | colk[nb] | prow[nb] | ri[blockDim] | perm[nb] | A (16-aligned)
-  double* rv = reinterpret_cast<double*>(smem_raw);
-  T* colk = reinterpret_cast<T*>(rv + blockDim.x);
-  T* prow = colk + nb;
-  int* ri = reinterpret_cast<int*>(prow + nb);
-  int* perm = ri + blockDim.x;
-  T* As = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(perm + nb) + 15) & ~uintptr_t(15));
-  const int nn = nb * nb;
-  for (long b = blockIdx.x; b < nblk; b += gridDim.x) {
-    T* Ag = blocks + (size_t)b * nn;
-    T* A = use_smem ? As : Ag;
-    if (use_smem) {
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) A[t] = Ag[t];
-      __syncthreads();
-    }
-    bool bad = false;
-    for (int k = 0; k < nb; ++k) {
-      // pivot search
-      double best = -1.0;
-      int bi = nb;
-      for (int i = k + threadIdx.x; i < nb; i += blockDim.x) {
-        double a = fabs((double)A[(size_t)i * nb + k]);
-        if (a > best || (a == best && i < bi)) {
-          best = a;
-          bi = i;
-        }
-      }
-      rv[threadIdx.x] = best;
-      ri[threadIdx.x] = bi;
-      __syncthreads();
-      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-          double a = rv[threadIdx.x + s];
-          int ia = ri[threadIdx.x + s];
-          if (a > rv[threadIdx.x] || (a == rv[threadIdx.x] && ia < ri[threadIdx.x])) {
-            rv[threadIdx.x] = a;
-            ri[threadIdx.x] = ia;
-          }
-        }
-        __syncthreads();
-      }
-      int p = ri[0];
-      double pa = rv[0];
-      __syncthreads();
-      if (!(pa > 0.0) || p >= nb) {
-        bad = true;
-        p = k;
-      }
-      if (threadIdx.x == 0) perm[k] = p;
-      if (p != k)
-        for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-          T x = A[(size_t)k * nb + j];
-          A[(size_t)k * nb + j] = A[(size_t)p * nb + j];
-          A[(size_t)p * nb + j] = x;
-        }
-      __syncthreads();
-      T piv = A[(size_t)k * nb + k];
-      if (bad) piv = T(1);
-      T ipiv = T(1) / piv;
-      for (int j = threadIdx.x; j < nb; j += blockDim.x) prow[j] = (j == k ? T(1) : A[(size_t)k * nb + j]) * ipiv;
-      for (int i = threadIdx.x; i < nb; i += blockDim.x) colk[i] = (i == k) ? T(0) : A[(size_t)i * nb + k];
-      __syncthreads();
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        int i = t / nb, j = t % nb;
-        if (i == k) {
-          A[t] = prow[j];
-        } else {
-          T a = (j == k) ? T(0) : A[t];
-          A[t] = a - colk[i] * prow[j];
-        }
-      }
-      __syncthreads();
-    }
-    // undo the row interchanges on the columns, last first
-    for (int k = nb - 1; k >= 0; --k) {
-      int p = perm[k];
-      if (p != k)
-        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-          T x = A[(size_t)i * nb + k];
-          A[(size_t)i * nb + k] = A[(size_t)i * nb + p];
-          A[(size_t)i * nb + p] = x;
-        }
-      __syncthreads();
-    }
-    if (bad && threadIdx.x == 0) atomicOr(status, ST_SINGULAR);
-    if (use_smem) {
-      for (int t = threadIdx.x; t < nn; t += blockDim.x) Ag[t] = A[t];
-    }
-    __syncthreads();
-  }
-}
-
-template <class T>
-cudaError_t launch_block_inverse(T* A, int nb, long nblk, int* status, cudaStream_t st) {
-  if (nblk <= 0) return cudaSuccess;
-  const int threads = 256;
-  size_t base = (2 * nb + 2) * sizeof(T) + threads * (sizeof(double) + sizeof(int)) + (nb + 4) * sizeof(int) + 32;
-  size_t full = base + (size_t)nb * nb * sizeof(T);
-  int use_smem = full <= 200 * 1024;
-  size_t smem = use_smem ? full : base;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(block_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  long grid = std::min<long>(nblk, 16L * num_sms());
-  note_launch();
-  block_inverse_kernel<T><<<(int)grid, threads, smem, st>>>(A, nb, nblk, use_smem, status);
-  return cudaGetLastError();
-}
-template cudaError_t launch_block_inverse<double>(double*, int, long, int*, cudaStream_t);
-template cudaError_t launch_block_inverse<float>(float*, int, long, int*, cudaStream_t);
-
 // ---------------------------------------------------------------- truncation
 template <class T>
 __global__ void truncate_kernel(const T* __restrict__ src, int nms, T* __restrict__ dst, int nmt, int m,
