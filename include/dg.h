@@ -110,14 +110,19 @@ dg_status dg_residual_noalloc(dg_mesh mesh, const double* W, const double* S, do
 #define DG_JVP_EXACT 0      /* forward-mode derivative of the discrete residual */
 #define DG_JVP_FD 1         /* eq. DG-mf with h = eps sqrt(1 + ||v||)/||W|| as printed */
 #define DG_JVP_FD_SCALED 2  /* eq. DG-mf with h = eps sqrt(1 + ||W||)/||v|| */
+#define DG_JVP_EXACT_FP32 3 /* exact linearisation evaluated in FP32 (the operator of
+                               the mixed-precision smoother on the finest level) */
 
 /* Kv = sigma M v + dR/dW(W) v: the product of the iteration matrix
  * K = M/(a_ii dt) + dR/dW of eq. ODEDG with a vector (Sec. 5.1), sigma being
  * the shift (1/(a_ii dt) for ESDIRK, 3/(2 dt) for BDF2) and M = |J| I.
  * DG_JVP_EXACT: exact linearisation (default).  DG_JVP_FD / _SCALED: the
  * matrix-free finite difference of eq. DG-mf with eps = 1e-7; R_W = R(W) must
- * then be given (device), else it may be NULL.  W, v, Kv: device FP64; Kv must
- * not alias W or v. */
+ * then be given (device), else it may be NULL.  DG_JVP_EXACT_FP32: W and v
+ * rounded to FP32, the exact linearisation in FP32, Kv widened to FP64 (Sec. 6:
+ * the inexact operator the mixed-precision preconditioner uses).  The FD and
+ * FP32 modes use the mesh handle's scratch: such calls on one mesh must not
+ * overlap.  W, v, Kv: device FP64; Kv must not alias W or v. */
 dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma,
                  const double* v, double* Kv, int mode, void* stream);
 

@@ -15,7 +15,7 @@ DG_OK = 0
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID", 2: "DG_ERR_OOM", 3: "DG_ERR_CUDA",
                 4: "DG_ERR_NONPHYSICAL", 5: "DG_ERR_NOT_CONVERGED", 6: "DG_ERR_BREAKDOWN",
                 7: "DG_ERR_TIMEOUT", 8: "DG_ERR_UNSUPPORTED"}
-JVP_EXACT, JVP_FD, JVP_FD_SCALED = 0, 1, 2
+JVP_EXACT, JVP_FD, JVP_FD_SCALED, JVP_EXACT_FP32 = 0, 1, 2, 3
 CYCLE_FMG, CYCLE_V, CYCLE_BJ = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR, BLOCKS_DIAG = 0, 1, 2

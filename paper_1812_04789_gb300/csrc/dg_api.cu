@@ -268,6 +268,15 @@ extern "C" dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, do
     CK(launch_residual<double>(mesh->m, W, v, nullptr, sigma, true, Kv, st));
     return DG_OK;
   }
+  if (mode == DG_JVP_EXACT_FP32) {   // the mixed-precision smoother's operator
+    const Mesh& M = mesh->m;
+    const long N = (long)M.E * M.nb;
+    CK(launch_convert<double, float>(N, W, M.t32.fd_w, st));
+    CK(launch_convert<double, float>(N, v, M.t32.fd_r, st));
+    CK(launch_residual<float>(M, M.t32.fd_w, M.t32.fd_r, nullptr, (float)sigma, true, M.t32.fd_o, st));
+    CK(launch_convert<float, double>(N, M.t32.fd_o, Kv, st));
+    return DG_OK;
+  }
   if (mode != DG_JVP_FD && mode != DG_JVP_FD_SCALED) return DG_ERR_INVALID;
   if (!R_W || R_W == Kv) return DG_ERR_INVALID;
   CK(fd_jvp(mesh->m, W, R_W, sigma, v, Kv, mode == DG_JVP_FD ? 0 : 1, st));

@@ -27,6 +27,7 @@ struct Tables {
   T* slots = nullptr;        // face slots [E][d][2][nb]
   T* fd_w = nullptr;         // finite-difference JVP scratch: W + h v
   T* fd_r = nullptr;         // finite-difference JVP scratch: R(W + h v)
+  T* fd_o = nullptr;         // FP32 JVP mode scratch: the product before conversion
 };
 
 // Plan of the tensor-core block probe (FP32 blocks): seed variables are taken

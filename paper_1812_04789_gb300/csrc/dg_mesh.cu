@@ -115,6 +115,8 @@ static cudaError_t upload_tables(Mesh& M, Tables<T>& t, const std::vector<double
   M.allocs.push_back(t.fd_w);
   if ((e = cudaMalloc((void**)&t.fd_r, nd * sizeof(T))) != cudaSuccess) return e;
   M.allocs.push_back(t.fd_r);
+  if ((e = cudaMalloc((void**)&t.fd_o, nd * sizeof(T))) != cudaSuccess) return e;
+  M.allocs.push_back(t.fd_o);
   return cudaSuccess;
 }
 

@@ -16,6 +16,9 @@
 //                plus sigma |J| v for a JVP or minus a source for a residual.
 // With S = Dual<T> the same code carries the directional derivative: the JVP
 // is the exact linearisation of the discrete residual.
+#include <algorithm>
+#include <type_traits>
+
 #include "dg_internal.h"
 
 namespace dgk {
@@ -257,6 +260,126 @@ __global__ void __launch_bounds__(256) volume_kernel(MeshView<T> mv, Phys<T> ph,
   }
 }
 
+// FP32 volume kernel with the basis tables in shared memory: one persistent
+// CTA per SM stages Tab[0][i][q] = phi_i(q) and Tab[1+k][i][q] = d phi_i/dx_k (q)
+// once (q padded to an odd stride, so that the projection's column reads are
+// free of bank conflicts), then NSLOT independent groups of 256 threads each
+// walk over elements, synchronising only among themselves (named barriers).
+// The same three phases as volume_kernel: interpolation (thread per point),
+// F_c + F_v, projection (thread per (v, i)) plus the face slots.
+template <int D, bool JVP, int NSLOT>
+__global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<float> mv, Phys<float> ph,
+                                                                   const float* __restrict__ W,
+                                                                   const float* __restrict__ V,
+                                                                   const float* __restrict__ slots,
+                                                                   const float* __restrict__ Src, float sigma,
+                                                                   float* __restrict__ out, int* status,
+                                                                   int nqp) {
+  using T = float;
+  using S = typename std::conditional<JVP, Dual<T>, T>::type;
+  constexpr int M = D + 2, NT = 1 + D;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = mv.nb, nm = mv.nm, nq = mv.nq, E = mv.E;
+  T* Tab = reinterpret_cast<T*>(smem_raw);            // [1 + D][nm][nqp]
+  T* sw = Tab + (size_t)NT * nm * nqp;                 // [nq] weights * |J|
+  const size_t per_slot = (size_t)nb * (JVP ? 2 : 1) + (size_t)nq * M * D;
+  for (int t = threadIdx.x; t < NT * nm * nq; t += blockDim.x) {
+    const int r = t / nq, q = t - r * nq;               // r = kk * nm + i
+    const int kk = r / nm, i = r - kk * nm;
+    Tab[(size_t)r * nqp + q] = kk == 0 ? mv.vphiT[(size_t)i * nq + q]
+                                       : mv.vdphiT[((size_t)(kk - 1) * nm + i) * nq + q];
+  }
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) sw[t] = mv.vw[t];
+  __syncthreads();
+  const int slot = threadIdx.x >> 8, tid = threadIdx.x & 255;
+  T* sW = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(sw + nq) + 15) & ~uintptr_t(15)) +
+       (size_t)slot * ((per_slot + 3) / 4 * 4);
+  T* sV = sW + nb;
+  T* sF = sV + (JVP ? nb : 0);                          // [nq][M][D]
+  const int bar = 1 + slot;
+  for (int e = blockIdx.x * NSLOT + slot; e < E; e += gridDim.x * NSLOT) {
+    for (int t = tid; t < nb; t += 256) {
+      sW[t] = W[(size_t)e * nb + t];
+      if (JVP) sV[t] = V[(size_t)e * nb + t];
+    }
+    asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
+    for (int q = tid; q < nq; q += 256) {
+      S u[M], g[M][D];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        u[v] = T(0);
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) g[v][kk] = T(0);
+      }
+      const T* tq = Tab + q;
+      for (int i = 0; i < nm; ++i) {
+        const T p = tq[(size_t)i * nqp];
+        T dp[D];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) dp[kk] = tq[((size_t)(1 + kk) * nm + i) * nqp];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          S a;
+          if constexpr (JVP) a = S(sW[v * nm + i], sV[v * nm + i]);
+          else a = sW[v * nm + i];
+          u[v] = u[v] + a * p;
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) g[v][kk] = g[v][kk] + a * dp[kk];
+        }
+      }
+      if (!physical<D>(u, ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
+      S F[M][D];
+      flux_total<D, S, T>(u, g, F, ph);
+      const T wq = sw[q];
+      T* fo = sF + (size_t)q * M * D;
+#pragma unroll
+      for (int v = 0; v < M; ++v)
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) fo[v * D + kk] = wq * (JVP ? tan_part(F[v][kk]) : val(F[v][kk]));
+    }
+    asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
+    for (int j = tid; j < nb; j += 256) {
+      const int v = j / nm, i = j - v * nm;
+      T acc[D];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) acc[kk] = T(0);
+      const T* fv = sF + v * D;
+      for (int q = 0; q < nq; ++q) {
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) acc[kk] += Tab[((size_t)(1 + kk) * nm + i) * nqp + q] * fv[(size_t)q * M * D + kk];
+      }
+      T a = T(0);
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) a -= acc[kk];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int em = mv.nbr[(e * D + k) * 2 + 0];
+        a += slots[(((size_t)e * D + k) * 2 + 0) * nb + j];
+        a += slots[(((size_t)em * D + k) * 2 + 1) * nb + j];
+      }
+      if (JVP) a += sigma * mv.detJ * sV[j];
+      else if (Src) a -= Src[(size_t)e * nb + j];
+      out[(size_t)e * nb + j] = a;
+    }
+    asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
+  }
+}
+
+constexpr int VOL_SLOTS = 3;
+
+// Shared memory of volume_kernel_st (FP32), when the tables fit beside the slots.
+static bool vol_tables_fit(const Mesh& M, bool jvp, size_t* bytes, int* nqp) {
+  if (M.nb > 256) return false;
+  *nqp = M.nq | 1;
+  const size_t per_slot = (size_t)M.nb * (jvp ? 2 : 1) + (size_t)M.nq * M.m * M.d;
+  const size_t n = (size_t)(1 + M.d) * M.nm * *nqp + M.nq;
+  *bytes = n * sizeof(float) + 16 + VOL_SLOTS * ((per_slot + 3) / 4 * 4) * sizeof(float);
+  int dev = 0, smax = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return *bytes <= (size_t)smax;
+}
+
 template <class T>
 static size_t face_smem(const Mesh& M, int fpc, bool jvp) {
   return sizeof(T) * (size_t)fpc *
@@ -283,6 +406,22 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
   face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if constexpr (std::is_same<T, float>::value) {
+    size_t tsm;
+    int nqp;
+    if (vol_tables_fit(Ms, JVP, &tsm, &nqp)) {
+      cudaFuncSetAttribute(volume_kernel_st<D, JVP, VOL_SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tsm);
+      int dev = 0, nsm = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const int grid = std::min(nsm, (Ms.E + VOL_SLOTS - 1) / VOL_SLOTS);
+      note_launch();
+      volume_kernel_st<D, JVP, VOL_SLOTS><<<grid, 256 * VOL_SLOTS, tsm, st>>>(mv, ph, W, V, slots, S, sigma, out,
+                                                                             Ms.status, nqp);
+      return cudaGetLastError();
+    }
+  }
   int epc = std::max(1, 256 / Ms.nq);
   size_t vsm = vol_smem<T>(Ms, epc, JVP);
   while (vsm > 200 * 1024 && epc > 1) vsm = vol_smem<T>(Ms, --epc, JVP);

@@ -86,6 +86,28 @@ def test_residual_source_and_free_stream():
     assert relmax(R.cpu().numpy(), -S) <= 1e-13
 
 
+@pytest.mark.parametrize("name", ["tgv3d_p4_3x3x3", "tgv3d_p2_3x2x4", "vortex2d_p5_3x4", "tgv3d_p1_1x2x5",
+                                  "tgv3d_p6_2x2x2"])
+def test_jvp_fp32_mode(name):
+    """The FP32 exact JVP (the fine-level smoother operator of the mixed
+    preconditioner) against the FP64 oracle.  Bar 2e-5 in the relative
+    max-norm: W and v rounded to FP32 (2^-24) and sums of ~10^3 terms per
+    output whose volume and face parts largely cancel."""
+    cfg = CASES[name]
+    om, oph = oracle_mesh(cfg), oracle_physics(cfg)
+    W = wl.perturbed_state(cfg, amp=0.05)
+    v = wl.random_vector(W.shape)
+    sigma = 1.5 / wl.time_step(cfg)
+    ref = o_jvp(om, oph, W, v, sigma)
+    m = gpu_mesh(cfg)
+    out = torch.empty(W.shape, dtype=torch.float64, device="cuda")
+    m.jvp(dev(W), dev(v), out, sigma, mode=B.JVP_EXACT_FP32)
+    assert m.status_sync() == B.DG_OK
+    err = relmax(out.cpu().numpy(), ref)
+    print("%s: FP32 JVP rel max err %.3e" % (name, err))
+    assert err <= 2e-5
+
+
 @pytest.mark.parametrize("mode,variant", [(B.JVP_FD, "printed"), (B.JVP_FD_SCALED, "scaled")])
 def test_jvp_fd_modes(mode, variant):
     cfg = CASES["vortex2d_p2_5x7"]
