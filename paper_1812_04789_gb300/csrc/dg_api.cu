@@ -105,7 +105,7 @@ cudaError_t MG<T>::smooth(int l, const T* b, T* x, int nu, cudaStream_t st) {
   CKE(launch_axpby<T>(L.N, 1.0, b, -1.0, L.r, st));           // r = b - A x
   CKE(K.start(L.r, st));
   for (int j = 0; j < nu; ++j) {
-    CKE(launch_block_apply<T>(L.Dinv, K.Vj(j), K.Zj(j), L.nb, mesh->E, st));
+    CKE(launch_block_apply<T>(L.Dinv, L.bs, L.inv_t, K.Vj(j), K.Zj(j), L.nb, mesh->E, st));
     CKE(op(l, K.Zj(j), K.w, st));
     CKE(K.arnoldi(j, st));
   }
@@ -134,7 +134,8 @@ template <class T>
 cudaError_t MG<T>::apply(const T* r, T* z, cudaStream_t st) {
   const int Lc = (int)lv.size() - 1;
   const long nev = (long)mesh->E * mesh->m;
-  if (cycle == DG_CYCLE_BJ) return launch_block_apply<T>(lv[0].Dinv, r, z, lv[0].nb, mesh->E, st);
+  if (cycle == DG_CYCLE_BJ)
+    return launch_block_apply<T>(lv[0].Dinv, lv[0].bs, lv[0].inv_t, r, z, lv[0].nb, mesh->E, st);
   if (cycle == DG_CYCLE_V) {
     CKE(cudaMemcpyAsync(lv[0].b, r, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st));
     CKE(cudaMemsetAsync(lv[0].x, 0, sizeof(T) * lv[0].N, st));
@@ -188,7 +189,8 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
     L.nu_pre = o.nu_pre[l];
     L.nu_post = o.nu_post[l];
     size_t nbl = (size_t)M.E * L.nb * L.nb;
-    CK(dalloc(mg.allocs, (void**)&L.Dinv, sizeof(T) * nbl, &h->block_bytes));
+    L.bs = (size_t)L.nb * inv_ld<T>(L.nb);
+    CK(dalloc(mg.allocs, (void**)&L.Dinv, sizeof(T) * (size_t)M.E * L.bs, &h->block_bytes));
     if (l >= 1) {
       CK(dalloc(mg.allocs, (void**)&L.Dop, sizeof(T) * nbl, &h->block_bytes));
       CK(dalloc(mg.allocs, (void**)&L.O, sizeof(T) * nbl * 2 * M.d, &h->block_bytes));
@@ -226,16 +228,19 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
     CK(cudaMemcpyAsync(mg.W, W64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
   else
     CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
-  CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, nl > 1 ? mg.lv[1].O : nullptr,
+  CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, mg.lv[0].bs, nl > 1 ? mg.lv[1].O : nullptr,
                             nl > 1 ? mg.lv[1].nm : 0, mg.scratch, mg.scratch_elems, st));
   for (int l = 1; l < nl; ++l) {
     Level<T>& L = mg.lv[l];
-    CK(launch_truncate_blocks<T>(mg.lv[0].Dinv, mg.lv[0].nm, L.Dop, L.nm, M.m, M.E, st));
+    CK(launch_truncate_blocks<T>(mg.lv[0].Dinv, mg.lv[0].nm, mg.lv[0].bs, L.Dop, L.nm, M.m, M.E, st));
     if (l >= 2)
-      CK(launch_truncate_blocks<T>(mg.lv[1].O, mg.lv[1].nm, L.O, L.nm, M.m, (long)M.E * 2 * M.d, st));
-    CK(cudaMemcpyAsync(L.Dinv, L.Dop, sizeof(T) * (size_t)M.E * L.nb * L.nb, cudaMemcpyDeviceToDevice, st));
+      CK(launch_truncate_blocks<T>(mg.lv[1].O, mg.lv[1].nm, (size_t)mg.lv[1].nb * mg.lv[1].nb, L.O, L.nm, M.m,
+                                   (long)M.E * 2 * M.d, st));
+    CK(cudaMemcpy2DAsync(L.Dinv, sizeof(T) * L.bs, L.Dop, sizeof(T) * L.nb * L.nb, sizeof(T) * L.nb * L.nb, M.E,
+                         cudaMemcpyDeviceToDevice, st));
   }
-  for (int l = 0; l < nl; ++l) CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, M.E, M.status, st));
+  for (int l = 0; l < nl; ++l)
+    CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, mg.lv[l].bs, M.E, M.status, &mg.lv[l].inv_t, st));
   return DG_OK;
 }
 
@@ -459,9 +464,19 @@ extern "C" dg_status dg_pmg_export_blocks(dg_pmg h, int level, int which, void* 
   int nb = h->precision == DG_PREC_FP64 ? h->mg64.lv[level].nb : h->mg32.lv[level].nb;
   const void* src;
   size_t cnt;
-  if (which == DG_BLOCKS_DIAG_INV) {
-    src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].Dinv : (const void*)h->mg32.lv[level].Dinv;
+  if (which == DG_BLOCKS_DIAG_INV) {   // unpacked to row-major nb x nb blocks
     cnt = (size_t)M.E * nb * nb;
+    if (out_bytes < cnt * es) return DG_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->precision == DG_PREC_FP64) {
+      const Level<double>& L = h->mg64.lv[level];
+      CK(launch_unpack_inverse<double>(L.Dinv, L.bs, L.inv_t, (double*)out, nb, M.E, st));
+    } else {
+      const Level<float>& L = h->mg32.lv[level];
+      CK(launch_unpack_inverse<float>(L.Dinv, L.bs, L.inv_t, (float*)out, nb, M.E, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return DG_OK;
   } else if (which == DG_BLOCKS_NEIGHBOUR) {
     if (level < 1) return DG_ERR_INVALID;
     src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].O : (const void*)h->mg32.lv[level].O;
@@ -472,11 +487,11 @@ extern "C" dg_status dg_pmg_export_blocks(dg_pmg h, int level, int which, void* 
     cudaStream_t st = (cudaStream_t)stream;
     if (level == 0) {   // the fine-level probe again, at the stored state and shift
       if (h->precision == DG_PREC_FP64)
-        CK(launch_probe_blocks<double>(M, h->mg64.W, h->sigma, (double*)out, nullptr, 0, h->mg64.scratch,
-                                       h->mg64.scratch_elems, st));
+        CK(launch_probe_blocks<double>(M, h->mg64.W, h->sigma, (double*)out, (size_t)nb * nb, nullptr, 0,
+                                       h->mg64.scratch, h->mg64.scratch_elems, st));
       else
-        CK(launch_probe_blocks<float>(M, h->mg32.W, (float)h->sigma, (float*)out, nullptr, 0, h->mg32.scratch,
-                                      h->mg32.scratch_elems, st));
+        CK(launch_probe_blocks<float>(M, h->mg32.W, (float)h->sigma, (float*)out, (size_t)nb * nb, nullptr, 0,
+                                      h->mg32.scratch, h->mg32.scratch_elems, st));
     } else {
       src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].Dop : (const void*)h->mg32.lv[level].Dop;
       CK(cudaMemcpyAsync(out, src, cnt * es, cudaMemcpyDeviceToDevice, st));

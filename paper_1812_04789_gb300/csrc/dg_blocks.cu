@@ -254,9 +254,9 @@ __device__ __forceinline__ void probe_sweep(const ProbeCtx<T>& cx, int task, int
 
 template <int D, class T>
 __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, const T* __restrict__ W,
-                                                    T sigma, T* __restrict__ Dout, T* __restrict__ Oout,
-                                                    int nmc, T* gscratch, int use_smem, int nbr_only,
-                                                    int* status) {
+                                                    T sigma, T* __restrict__ Dout, size_t dstride,
+                                                    T* __restrict__ Oout, int nmc, T* gscratch, int use_smem,
+                                                    int nbr_only, int* status) {
   constexpr int M = D + 2, NF = 2 * D, PU = M * (1 + D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = mv.nb, nm = mv.nm, nq = mv.nq, nqf = mv.nqf, E = mv.E;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) probe_kernel(MeshView<T> mv, Phys<T> ph, 
     int nbrs[NF];
 #pragma unroll
     for (int s = 0; s < NF; ++s) nbrs[s] = mv.nbr[e * NF + s];
-    T* De = Dout + (size_t)e * nb * nb;
+    T* De = Dout + (size_t)e * dstride;
     if (!nbr_only)
       for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) De[t] = (t / nb == t % nb) ? sigma * mv.detJ : T(0);
     if (Oout)
@@ -324,8 +324,8 @@ static int num_sms() {
 int probe_grid_global() { return 2 * num_sms(); }
 
 template <int D, class T>
-static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, T* Oout, int nmc, T* scratch,
-                             size_t scratch_elems, bool nbr_only, cudaStream_t st) {
+static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, size_t dstride, T* Oout, int nmc,
+                             T* scratch, size_t scratch_elems, bool nbr_only, cudaStream_t st) {
   bool fits;
   size_t tot = probe_scratch_elems<T>(Ms, nmc, &fits);
   int grid;
@@ -340,8 +340,8 @@ static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, T* Oo
     if (!scratch || scratch_elems < tot * (size_t)grid) return cudaErrorInvalidValue;
   }
   note_launch();
-  probe_kernel<D, T><<<grid, 256, smem, st>>>(Ms.view<T>(), Ms.phys_t<T>(), W, sigma, Dout, Oout, nmc,
-                                             scratch, fits ? 1 : 0, nbr_only ? 1 : 0, Ms.status);
+  probe_kernel<D, T><<<grid, 256, smem, st>>>(Ms.view<T>(), Ms.phys_t<T>(), W, sigma, Dout, dstride, Oout,
+                                             nmc, scratch, fits ? 1 : 0, nbr_only ? 1 : 0, Ms.status);
   return cudaGetLastError();
 }
 
@@ -355,29 +355,29 @@ static bool use_tc(const Mesh& M) {
 }
 
 template <class T>
-cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, T* O, int nmc, T* scratch,
-                                size_t scratch_elems, cudaStream_t st) {
+cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, size_t dstride, T* O, int nmc,
+                                T* scratch, size_t scratch_elems, cudaStream_t st) {
   bool nbr_only = false;
   if (std::is_same<T, float>::value && use_tc(M)) {
-    cudaError_t e = launch_probe_tc(M, (const float*)W, (float)sigma, (float*)D, st);
+    cudaError_t e = launch_probe_tc(M, (const float*)W, (float)sigma, (float*)D, dstride, st);
     if (e != cudaSuccess) return e;
     bool self = false;
     for (int k = 0; k < M.d; ++k) self = self || M.desc.n[k] == 1;
     if (O == nullptr && !self) return cudaSuccess;
     nbr_only = true;
   }
-  if (M.d == 2) return run_probe<2, T>(M, W, sigma, D, O, nmc, scratch, scratch_elems, nbr_only, st);
-  return run_probe<3, T>(M, W, sigma, D, O, nmc, scratch, scratch_elems, nbr_only, st);
+  if (M.d == 2) return run_probe<2, T>(M, W, sigma, D, dstride, O, nmc, scratch, scratch_elems, nbr_only, st);
+  return run_probe<3, T>(M, W, sigma, D, dstride, O, nmc, scratch, scratch_elems, nbr_only, st);
 }
-template cudaError_t launch_probe_blocks<double>(const Mesh&, const double*, double, double*, double*, int,
-                                                 double*, size_t, cudaStream_t);
-template cudaError_t launch_probe_blocks<float>(const Mesh&, const float*, float, float*, float*, int, float*,
-                                                size_t, cudaStream_t);
+template cudaError_t launch_probe_blocks<double>(const Mesh&, const double*, double, double*, size_t, double*,
+                                                 int, double*, size_t, cudaStream_t);
+template cudaError_t launch_probe_blocks<float>(const Mesh&, const float*, float, float*, size_t, float*, int,
+                                                float*, size_t, cudaStream_t);
 
 // ---------------------------------------------------------------- truncation
 template <class T>
-__global__ void truncate_kernel(const T* __restrict__ src, int nms, T* __restrict__ dst, int nmt, int m,
-                                long nblk) {
+__global__ void truncate_kernel(const T* __restrict__ src, int nms, size_t sstride, T* __restrict__ dst,
+                                int nmt, int m, long nblk) {
   const int nbs = m * nms, nbt = m * nmt;
   const long tot = nblk * nbt * nbt;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
@@ -385,21 +385,23 @@ __global__ void truncate_kernel(const T* __restrict__ src, int nms, T* __restric
     int r = (int)(t % ((long)nbt * nbt));
     int row = r / nbt, col = r % nbt;
     int v = row / nmt, i = row % nmt, w = col / nmt, j = col % nmt;
-    dst[t] = src[(size_t)b * nbs * nbs + (size_t)(v * nms + i) * nbs + (w * nms + j)];
+    dst[t] = src[(size_t)b * sstride + (size_t)(v * nms + i) * nbs + (w * nms + j)];
   }
 }
 
 template <class T>
-cudaError_t launch_truncate_blocks(const T* src, int nms, T* dst, int nmt, int m, long nblk, cudaStream_t st) {
+cudaError_t launch_truncate_blocks(const T* src, int nms, size_t sstride, T* dst, int nmt, int m, long nblk,
+                                   cudaStream_t st) {
   long tot = nblk * (long)(m * nmt) * (m * nmt);
   if (tot <= 0) return cudaSuccess;
   long grid = std::min<long>((tot + 255) / 256, 65535L * 8);
   note_launch();
-  truncate_kernel<T><<<(int)grid, 256, 0, st>>>(src, nms, dst, nmt, m, nblk);
+  truncate_kernel<T><<<(int)grid, 256, 0, st>>>(src, nms, sstride, dst, nmt, m, nblk);
   return cudaGetLastError();
 }
-template cudaError_t launch_truncate_blocks<double>(const double*, int, double*, int, int, long, cudaStream_t);
-template cudaError_t launch_truncate_blocks<float>(const float*, int, float*, int, int, long, cudaStream_t);
+template cudaError_t launch_truncate_blocks<double>(const double*, int, size_t, double*, int, int, long,
+                                                    cudaStream_t);
+template cudaError_t launch_truncate_blocks<float>(const float*, int, size_t, float*, int, int, long, cudaStream_t);
 
 // ---------------------------------------------------------------- block apply / BSR
 // One CTA per element: the element's input (and neighbours' for BSR) staged in
@@ -418,9 +420,9 @@ __device__ __forceinline__ void row_dot2(const T* __restrict__ A0, const T* __re
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, const T* __restrict__ O,
-                                                  const int* __restrict__ nbr, int nf, const T* __restrict__ x,
-                                                  T* __restrict__ y, int nb, int E) {
+__global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, size_t dstride,
+                                                  const T* __restrict__ O, const int* __restrict__ nbr, int nf,
+                                                  const T* __restrict__ x, T* __restrict__ y, int nb, int E) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);   // [(1 + nf)][nb]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -435,7 +437,8 @@ __global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, cons
     for (int r0 = 2 * warp; r0 < nb; r0 += 2 * nw) {
       const int r1 = min(r0 + 1, nb - 1);     // an odd last row is computed twice, stored once
       T s0 = T(0), s1 = T(0);
-      row_dot2<T>(Dm + ((size_t)e * nb + r0) * nb, Dm + ((size_t)e * nb + r1) * nb, xs, nb, lane, s0, s1);
+      row_dot2<T>(Dm + (size_t)e * dstride + (size_t)r0 * nb, Dm + (size_t)e * dstride + (size_t)r1 * nb, xs, nb,
+                  lane, s0, s1);
       if (O) {
         for (int s = 0; s < nf; ++s) {
           const T* Ob = O + ((size_t)e * nf + s) * nb * nb;
@@ -456,15 +459,111 @@ __global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, cons
   }
 }
 
+// Block-Jacobi apply on column-major inverses (leading dimension ld = inv_ld(nb)):
+// each thread owns 16 bytes of rows (4 FP32 or 2 FP64) of one element and
+// streams the columns with one vector load each (read-only, not kept in L1:
+// the blocks are read once per apply); `epc` elements per CTA pass share the
+// staged inputs.  No reductions: every thread finishes its own rows.
 template <class T>
-cudaError_t launch_block_apply(const T* A, const T* r, T* z, int nb, int E, cudaStream_t st) {
+struct Vec16;
+template <>
+struct Vec16<float> {
+  static constexpr int N = 4;
+  __device__ __forceinline__ static void load(const float* p, float* v) {
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+                 : "l"(p));
+  }
+};
+template <>
+struct Vec16<double> {
+  static constexpr int N = 2;
+  __device__ __forceinline__ static void load(const double* p, double* v) {
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "l"(p));
+  }
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) bj_colmajor_kernel(const T* __restrict__ A, size_t bstride,
+                                                          const T* __restrict__ x, T* __restrict__ y, int nb,
+                                                          int ld, int E, int epc, int tpe) {
+  constexpr int R = Vec16<T>::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);   // [epc][nb]
+  const int sub = threadIdx.x / tpe, tt = threadIdx.x - sub * tpe;
+  for (long e0 = (long)blockIdx.x * epc; e0 < E; e0 += (long)gridDim.x * epc) {
+    const int nl = (int)min((long)epc, E - e0);
+    for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) xs[t] = x[(size_t)e0 * nb + t];
+    __syncthreads();
+    if (sub < nl) {
+      const T* base = A + (size_t)(e0 + sub) * bstride + R * tt;
+      const T* xe = xs + (size_t)sub * nb;
+      T acc[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[j] = T(0);
+#pragma unroll 8
+      for (int c = 0; c < nb; ++c) {
+        T a[R];
+        Vec16<T>::load(base + (size_t)c * ld, a);
+        const T xv = xe[c];
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[j] += a[j] * xv;
+      }
+      T* yo = y + (size_t)(e0 + sub) * nb + R * tt;
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (R * tt + j < nb) yo[j] = acc[j];
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+cudaError_t launch_block_apply(const T* A, size_t bstride, int transposed, const T* r, T* z, int nb, int E,
+                               cudaStream_t st) {
+  if (transposed) {
+    const int ld = inv_ld<T>(nb), tpe = ld / Vec16<T>::N;
+    const int epc = std::max(1, 256 / tpe);
+    const int threads = (epc * tpe + 31) / 32 * 32;
+    const int grid = std::min((E + epc - 1) / epc, 8 * num_sms());
+    note_launch();
+    bj_colmajor_kernel<T><<<grid, threads, (size_t)epc * nb * sizeof(T), st>>>(A, bstride, r, z, nb, ld, E, epc,
+                                                                                tpe);
+    return cudaGetLastError();
+  }
   int grid = std::min(E, 32 * num_sms());
   note_launch();
-  bsr_kernel<T><<<grid, 256, nb * sizeof(T), st>>>(A, nullptr, nullptr, 0, r, z, nb, E);
+  bsr_kernel<T><<<grid, 256, nb * sizeof(T), st>>>(A, bstride, nullptr, nullptr, 0, r, z, nb, E);
   return cudaGetLastError();
 }
-template cudaError_t launch_block_apply<double>(const double*, const double*, double*, int, int, cudaStream_t);
-template cudaError_t launch_block_apply<float>(const float*, const float*, float*, int, int, cudaStream_t);
+template cudaError_t launch_block_apply<double>(const double*, size_t, int, const double*, double*, int, int,
+                                                cudaStream_t);
+template cudaError_t launch_block_apply<float>(const float*, size_t, int, const float*, float*, int, int,
+                                               cudaStream_t);
+
+template <class T>
+__global__ void unpack_inverse_kernel(const T* __restrict__ A, size_t bstride, int transposed, T* __restrict__ out,
+                                      int nb, int ld, long nblk) {
+  const long tot = nblk * nb * nb;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / ((long)nb * nb);
+    const int rc = (int)(t - b * nb * nb), r = rc / nb, c = rc - r * nb;
+    out[t] = A[(size_t)b * bstride + (transposed ? (size_t)c * ld + r : (size_t)r * nb + c)];
+  }
+}
+
+template <class T>
+cudaError_t launch_unpack_inverse(const T* A, size_t bstride, int transposed, T* out, int nb, long nblk,
+                                  cudaStream_t st) {
+  const long tot = nblk * (long)nb * nb;
+  if (tot <= 0) return cudaSuccess;
+  note_launch();
+  unpack_inverse_kernel<T><<<(int)std::min<long>((tot + 255) / 256, 65535L * 8), 256, 0, st>>>(
+      A, bstride, transposed, out, nb, inv_ld<T>(nb), nblk);
+  return cudaGetLastError();
+}
+template cudaError_t launch_unpack_inverse<double>(const double*, size_t, int, double*, int, long, cudaStream_t);
+template cudaError_t launch_unpack_inverse<float>(const float*, size_t, int, float*, int, long, cudaStream_t);
 
 template <class T>
 cudaError_t launch_bsr(const T* D, const T* O, const int* nbr, int d, const T* x, T* y, int nb, int E,
@@ -472,7 +571,7 @@ cudaError_t launch_bsr(const T* D, const T* O, const int* nbr, int d, const T* x
   int grid = std::min(E, 32 * num_sms());
   size_t smem = (size_t)(1 + 2 * d) * nb * sizeof(T);
   note_launch();
-  bsr_kernel<T><<<grid, 256, smem, st>>>(D, O, nbr, 2 * d, x, y, nb, E);
+  bsr_kernel<T><<<grid, 256, smem, st>>>(D, (size_t)nb * nb, O, nbr, 2 * d, x, y, nb, E);
   return cudaGetLastError();
 }
 template cudaError_t launch_bsr<double>(const double*, const double*, const int*, int, const double*, double*,

@@ -76,8 +76,9 @@ cudaError_t launch_residual_with_slots(const Mesh& M, const double* W, const dou
 // Element Jacobian blocks by probing: D[e] = dR_e/dW_e + sigma |J| I (nb x nb),
 // and when O != nullptr the neighbour blocks O[e][2k+side] restricted to the
 // first nmc modes of every variable (nbc x nbc, nbc = m nmc).
+// D[e] starts at D + e * dstride (row-major, row stride nb).
 template <class T>
-cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, T* O, int nmc,
+cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, size_t dstride, T* O, int nmc,
                                 T* scratch, size_t scratch_elems, cudaStream_t st);
 template <class T>
 size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem);
@@ -85,21 +86,40 @@ size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem);
 // Tensor-core probe of the FP32 diagonal blocks: D[e] = dR_e/dW_e (volume and
 // own-face seeds) + sigma |J| I, written in full.  Neighbour-seeded terms are
 // the SIMT kernel's.  build_tc_tables fills the mesh's tables (M.tc.ok).
-cudaError_t launch_probe_tc(const Mesh& M, const float* W, float sigma, float* D, cudaStream_t st);
+cudaError_t launch_probe_tc(const Mesh& M, const float* W, float sigma, float* D, size_t dstride,
+                            cudaStream_t st);
 cudaError_t build_tc_tables(Mesh& M);
 
-// Batched in-place inverse of nblk blocks of size nb (Gauss-Jordan, partial pivoting).
+// Batched in-place inverse of nblk row-major blocks of size nb starting bstride
+// elements apart (bstride >= nb * inv_ld(nb)).  *transposed = 1 when the
+// inverse is stored column-major with leading dimension inv_ld(nb) (rows
+// padded to a 16-byte multiple, the layout the block-Jacobi apply streams with
+// vector loads), 0 when it stays row-major (blocks too large for registers or
+// shared memory).  Gauss-Jordan, partial pivoting.
 template <class T>
-cudaError_t launch_block_inverse(T* A, int nb, long nblk, int* status, cudaStream_t st);
+constexpr int inv_ld(int nb) {
+  return (nb + (int)(16 / sizeof(T)) - 1) / (int)(16 / sizeof(T)) * (int)(16 / sizeof(T));
+}
+template <class T>
+cudaError_t launch_block_inverse(T* A, int nb, size_t bstride, long nblk, int* status, int* transposed,
+                                 cudaStream_t st);
 
 // Leading sub-block per variable pair: dst[b] (m nmt)^2 from src[b] (m nms)^2.
+// Source blocks start sstride elements apart (row-major, row stride m nms).
 template <class T>
-cudaError_t launch_truncate_blocks(const T* src, int nms, T* dst, int nmt, int m, long nblk,
+cudaError_t launch_truncate_blocks(const T* src, int nms, size_t sstride, T* dst, int nmt, int m, long nblk,
                                    cudaStream_t st);
 
-// z[e] = Ainv[e] r[e]
+// z[e] = Ainv[e] r[e]; blocks bstride apart, column-major with leading
+// dimension inv_ld(nb) when transposed, else row-major.
 template <class T>
-cudaError_t launch_block_apply(const T* A, const T* r, T* z, int nb, int E, cudaStream_t st);
+cudaError_t launch_block_apply(const T* A, size_t bstride, int transposed, const T* r, T* z, int nb, int E,
+                               cudaStream_t st);
+
+// Row-major copy (nb x nb per block, packed) of inverse blocks in the layout above.
+template <class T>
+cudaError_t launch_unpack_inverse(const T* A, size_t bstride, int transposed, T* out, int nb, long nblk,
+                                  cudaStream_t st);
 
 // y = D x + sum_s O_s x_nbr(s)
 template <class T>
@@ -152,7 +172,9 @@ template <class T>
 struct Level {
   int p = 0, nm = 0, nb = 0;
   long N = 0;
-  T* Dinv = nullptr;         // inverse diagonal blocks [E][nb][nb]
+  T* Dinv = nullptr;         // inverse diagonal blocks, E blocks bs apart (see launch_block_inverse)
+  size_t bs = 0;             // block stride of Dinv: nb * inv_ld<T>(nb)
+  int inv_t = 0;             // Dinv column-major (1) or row-major (0)
   T* Dop = nullptr;          // diagonal blocks of the inherited operator (l >= 1)
   T* O = nullptr;            // neighbour blocks [E][2d][nb][nb] (l >= 1)
   T *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;

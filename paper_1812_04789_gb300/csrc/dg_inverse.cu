@@ -11,12 +11,17 @@
 // was the pivot.  A zero pivot marks the status word (the block is singular)
 // and the step continues with pivot 1.
 //
+// Blocks come row-major, bstride elements apart.  The inverse leaves
+// column-major with leading dimension ld = inv_ld(nb) (rows padded to a
+// 16-byte multiple with zeros), the layout the block-Jacobi apply streams,
+// except from the in-place global-memory path, which leaves it row-major.
+//
 // block_inverse_reg_kernel (nb <= 16 R): 256 threads as a 16 x 16 grid;
 // thread (ty, tx) keeps the R x R entries of rows ty + 16 a and columns
 // tx + 16 b in registers for the whole elimination, so a step costs R^2 FMAs
 // per thread plus two shared-memory vectors (the pivot row and column) and
-// three barriers.  The permuted result is staged in shared memory and written
-// out coalesced.
+// three barriers.  The permuted, transposed result is staged in shared memory
+// and written out coalesced.
 // block_inverse_kernel (larger blocks): the block in shared memory (or global
 // memory when it does not fit), one warp per row in the update.
 #include <algorithm>
@@ -44,8 +49,8 @@ __device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
 }
 
 template <class T, int R>
-__global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict__ blocks, int nb, long nblk,
-                                                                   int* status) {
+__global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict__ blocks, int nb,
+                                                                   size_t bstride, long nblk, int* status) {
   constexpr int NP = 16 * R;
   __shared__ T colk[NP], prow[NP];
   __shared__ T cand_v[16], cand_s[16];
@@ -54,11 +59,11 @@ __global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict
   __shared__ int s_p;
   __shared__ T s_piv;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);   // nb * nb output staging
+  T* S = reinterpret_cast<T*>(smem_raw);   // nb * ld output staging (column-major)
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int nn = nb * nb;
+  const int ld = inv_ld<T>(nb), nl = nb * ld;
   for (long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    T* Ag = blocks + (size_t)blk * nn;
+    T* Ag = blocks + (size_t)blk * bstride;
     T t[R][R];
 #pragma unroll
     for (int a = 0; a < R; ++a)
@@ -182,10 +187,14 @@ __global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict
 #pragma unroll
       for (int b = 0; b < R; ++b) {
         const int i = ty + 16 * a, j = tx + 16 * b;
-        if (i < nb && j < nb) S[(size_t)step_of[i] * nb + piv_row[j]] = t[a][b];
+        if (i < nb && j < nb) S[(size_t)piv_row[j] * ld + step_of[i]] = t[a][b];
       }
+    for (int e = threadIdx.x; e < nb * (ld - nb); e += blockDim.x) {
+      const int c = e / (ld - nb);
+      S[(size_t)c * ld + nb + (e - c * (ld - nb))] = T(0);
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) Ag[e] = S[e];
+    for (int e = threadIdx.x; e < nl; e += blockDim.x) Ag[e] = S[e];
     if (bad && threadIdx.x == 0) atomicOr(status, ST_SINGULAR);
     __syncthreads();
   }
@@ -194,8 +203,8 @@ __global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict
 // Blocks too large for registers: the same elimination on a copy in shared
 // memory (or in place in global memory).  One warp per row in the update.
 template <class T>
-__global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ blocks, int nb, long nblk,
-                                                            int use_smem, int* status) {
+__global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ blocks, int nb, size_t bstride,
+                                                            long nblk, int use_smem, int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // byte layout: colk[nb] | prow[nb] | piv_row[nb] | step_of[nb] | used[nb] | lead[nb] | A (16-aligned)
   T* colk = reinterpret_cast<T*>(smem_raw);
@@ -211,8 +220,9 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ bloc
   T* As = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(lead + nb) + 15) & ~uintptr_t(15));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nn = nb * nb;
+  const int ld = inv_ld<T>(nb);
   for (long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    T* Ag = blocks + (size_t)blk * nn;
+    T* Ag = blocks + (size_t)blk * bstride;
     T* A = use_smem ? As : Ag;
     if (use_smem)
       for (int e = threadIdx.x; e < nn; e += blockDim.x) A[e] = Ag[e];
@@ -282,11 +292,15 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ bloc
       }
       __syncthreads();
     }
-    // permute into place through the output: X[step_of[i]][piv_row[j]] = R[i][j]
+    // permute into the output: X[step_of[i]][piv_row[j]] = R[i][j], column-major
     if (use_smem) {
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         const int i = e / nb, j = e - i * nb;
-        Ag[(size_t)step_of[i] * nb + piv_row[j]] = A[e];
+        Ag[(size_t)piv_row[j] * ld + step_of[i]] = A[e];
+      }
+      for (int e = threadIdx.x; e < nb * (ld - nb); e += blockDim.x) {
+        const int c = e / (ld - nb);
+        Ag[(size_t)c * ld + nb + (e - c * (ld - nb))] = T(0);
       }
     } else {
       // in place in global memory: the row permutation i -> step_of[i], then
@@ -335,32 +349,34 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ bloc
 }
 
 template <class T, int R>
-cudaError_t run_reg(T* A, int nb, long nblk, int* status, cudaStream_t st) {
-  const size_t smem = (size_t)nb * nb * sizeof(T);
+cudaError_t run_reg(T* A, int nb, size_t bstride, long nblk, int* status, cudaStream_t st) {
+  const size_t smem = (size_t)nb * inv_ld<T>(nb) * sizeof(T);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(block_inverse_reg_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_inverse_reg_kernel<T, R>, 256, smem);
   const long grid = std::min<long>(nblk, (long)std::max(1, occ) * num_sms_inv());
   note_launch();
-  block_inverse_reg_kernel<T, R><<<(int)grid, 256, smem, st>>>(A, nb, nblk, status);
+  block_inverse_reg_kernel<T, R><<<(int)grid, 256, smem, st>>>(A, nb, bstride, nblk, status);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 template <class T>
-cudaError_t launch_block_inverse(T* A, int nb, long nblk, int* status, cudaStream_t st) {
+cudaError_t launch_block_inverse(T* A, int nb, size_t bstride, long nblk, int* status, int* transposed,
+                                 cudaStream_t st) {
+  *transposed = 1;
   if (nblk <= 0) return cudaSuccess;
   // register tiles: R x R values of T per thread (at most 128 32-bit registers)
   const int R = (nb + 15) / 16;
   constexpr int RMAX = sizeof(T) == 4 ? 11 : 8;
   if (R <= RMAX) {
-    if (R <= 1) return run_reg<T, 1>(A, nb, nblk, status, st);
-    if (R <= 2) return run_reg<T, 2>(A, nb, nblk, status, st);
-    if (R <= 4) return run_reg<T, 4>(A, nb, nblk, status, st);
-    if (R <= 8) return run_reg<T, 8>(A, nb, nblk, status, st);
-    return run_reg<T, (RMAX > 8 ? RMAX : 8)>(A, nb, nblk, status, st);
+    if (R <= 1) return run_reg<T, 1>(A, nb, bstride, nblk, status, st);
+    if (R <= 2) return run_reg<T, 2>(A, nb, bstride, nblk, status, st);
+    if (R <= 4) return run_reg<T, 4>(A, nb, bstride, nblk, status, st);
+    if (R <= 8) return run_reg<T, 8>(A, nb, bstride, nblk, status, st);
+    return run_reg<T, (RMAX > 8 ? RMAX : 8)>(A, nb, bstride, nblk, status, st);
   }
   const int threads = 256;
   const size_t base = 2 * nb * sizeof(T) + 4 * nb * sizeof(int) + 32;
@@ -373,11 +389,12 @@ cudaError_t launch_block_inverse(T* A, int nb, long nblk, int* status, cudaStrea
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(block_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long grid = std::min<long>(nblk, (use_smem ? 1L : 8L) * num_sms_inv());
+  *transposed = use_smem;
   note_launch();
-  block_inverse_kernel<T><<<(int)grid, threads, smem, st>>>(A, nb, nblk, use_smem, status);
+  block_inverse_kernel<T><<<(int)grid, threads, smem, st>>>(A, nb, bstride, nblk, use_smem, status);
   return cudaGetLastError();
 }
-template cudaError_t launch_block_inverse<double>(double*, int, long, int*, cudaStream_t);
-template cudaError_t launch_block_inverse<float>(float*, int, long, int*, cudaStream_t);
+template cudaError_t launch_block_inverse<double>(double*, int, size_t, long, int*, int*, cudaStream_t);
+template cudaError_t launch_block_inverse<float>(float*, int, size_t, long, int*, int*, cudaStream_t);
 
 }  // namespace dgk

@@ -149,8 +149,8 @@ __device__ __forceinline__ void tc_produce(const float* __restrict__ Jb, const f
 template <int D>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     probe_tc_kernel(MeshView<float> mv, Phys<float> ph, const float* __restrict__ W, float sigma,
-                    float* __restrict__ Dout, const float* __restrict__ test, const float* __restrict__ trial,
-                    TcPlan P, int* status) {
+                    float* __restrict__ Dout, size_t dstride, const float* __restrict__ test,
+                    const float* __restrict__ trial, TcPlan P, int* status) {
   using namespace umma;
   constexpr int M = D + 2, NS = 1 + D, NF = 2 * D, KMX = 3 + D, PU = M * (1 + D);
   extern __shared__ __align__(128) unsigned char smem[];
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tmem_ld16(tmem + ((uint32_t)lb << 16) + (uint32_t)(ti * npad + c0), v16);
             if (r < rows) {
               const int pair = r / nm, ip = r - pair * nm, w = w0 + pair / M, v = pair % M;
-              float* drow = Dout + (size_t)e * nb * nb + (size_t)(v * nm + ip) * nb + (size_t)w * nm;
+              float* drow = Dout + (size_t)e * dstride + (size_t)(v * nm + ip) * nb + (size_t)w * nm;
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
                 const int i = c0 + j;
@@ -424,7 +424,8 @@ cudaError_t build_tc_tables(Mesh& M) {
 }
 
 template <int D>
-static cudaError_t run_tc(const Mesh& M, const float* W, float sigma, float* Dout, cudaStream_t st) {
+static cudaError_t run_tc(const Mesh& M, const float* W, float sigma, float* Dout, size_t dstride,
+                          cudaStream_t st) {
   const TcPlan& P = M.tc;
   // at most 512 / tmem_cols co-resident CTAs per SM may hold TMEM at once:
   // request enough shared memory that no more fit
@@ -440,13 +441,14 @@ static cudaError_t run_tc(const Mesh& M, const float* W, float sigma, float* Dou
   const int grid = std::min(M.E, num_sms_tc() * occ);
   note_launch();
   probe_tc_kernel<D><<<grid, TC_THREADS, smem, st>>>(M.view<float>(), M.phys_t<float>(), W, sigma, Dout,
-                                                     M.tc_test, M.tc_trial, P, M.status);
+                                                     dstride, M.tc_test, M.tc_trial, P, M.status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_probe_tc(const Mesh& M, const float* W, float sigma, float* D, cudaStream_t st) {
+cudaError_t launch_probe_tc(const Mesh& M, const float* W, float sigma, float* D, size_t dstride,
+                            cudaStream_t st) {
   if (!M.tc.ok) return cudaErrorInvalidValue;
-  return M.d == 2 ? run_tc<2>(M, W, sigma, D, st) : run_tc<3>(M, W, sigma, D, st);
+  return M.d == 2 ? run_tc<2>(M, W, sigma, D, dstride, st) : run_tc<3>(M, W, sigma, D, dstride, st);
 }
 
 }  // namespace dgk
