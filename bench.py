@@ -30,6 +30,7 @@ import numpy as np  # noqa: E402
 
 from paper_1812_04789_gb300 import workloads as wl  # noqa: E402
 
+BJ_KERNEL_VERSION = "colmajor-v1"   # bump when the block-Jacobi apply kernel changes
 METRIC = "Implicit-step DOFs/s (mixed vs FP64, 1 GB300); JVP % HBM roofline; p99 latency"
 UNIT = "DOFs/s"
 
@@ -207,6 +208,31 @@ def kernel_roofline(torch, B, stepper, stream, peaks):
     jb = E * nb * 8 * 3                      # read W and v, write Kv (FP64)
     out["jvp_fp64"] = dict(ms=ms, bytes=jb, gbs=jb / (ms * 1e-3) / 1e9,
                            hbm_frac=jb / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"])
+    # tensor-core block probe of the fine diagonal blocks: exporting the
+    # un-inverted level-0 blocks reruns exactly that kernel (no neighbour
+    # blocks are requested and no direction has a single element)
+    if stepper.opts.precision == B.PREC_MIXED and min(stepper.cfg["n"]) > 1:
+        D = torch.empty((E, nb, nb), dtype=torch.float32, device=r.device)
+        stepper.pmg.export_blocks(0, B.BLOCKS_DIAG, D, stream=stream)
+        ts = []
+        for _ in range(3):
+            e0.record(stream)
+            stepper.pmg.export_blocks(0, B.BLOCKS_DIAG, D, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        d, nm = len(stepper.cfg["n"]), mesh.nm
+        nq1 = stepper.cfg["p"] + 2
+        # the dense contraction D[(w,v,i'), i] += Z[(w,v,i'), K] Trial[i, K], one pass,
+        # K = (volume points + own-face points) x (1 + d)
+        K = (nq1 ** d + 2 * d * nq1 ** (d - 1)) * (1 + d)
+        flops = 2.0 * E * (mesh.m * mesh.m * nm) * nm * K
+        tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25     # nominal dense TF32 / BF16 ratio
+        out["probe_tc"] = dict(ms=ms, flops=flops, tflops=flops / (ms * 1e-3) / 1e12, peak_tflops=tf32_peak,
+                               frac=flops / (ms * 1e-3) / 1e12 / tf32_peak,
+                               peak_source="measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25")
+        del D
     return out
 
 
@@ -378,6 +404,12 @@ def run_gb300(args):
                    "h2d_bytes_per_step": int(hW0.numel() * 8 * 2), "d2h_bytes_per_step": int(hout.numel() * 8)}
     mixed = results["mixed"]
     bj = roof["bj_apply"]
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if os.path.exists(tf):
+        rec = json.load(open(tf)).get("bj_apply_mixed", {})
+        if rec.get("config") == args.config and rec.get("kernel_version") == BJ_KERNEL_VERSION:
+            traffic = rec.get("dram_bytes_per_launch")
     es = 4
     line = {
         "metric": METRIC, "value": mixed["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -395,12 +427,15 @@ def run_gb300(args):
                  "fgmres_iters_per_solve": results.get("fp64", {}).get("fgmres_iters_per_solve")},
         "fgmres_iters_per_solve": mixed["fgmres_iters_per_solve"],
         "mixed_vs_fp64_rel_l2": err, "mixed_vs_fp64_dW_rel_l2": err_dw,
-        "roofline": {"bound": "hbm", "kernel": "bsr_kernel<float> (fine block-Jacobi apply)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "bj_colmajor_kernel<float> (fine block-Jacobi apply; timed with the FP64<->FP32 "
+                               "conversions of its input and output, whose bytes are counted)",
                      "achieved": bj["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": bj["gbs"] / peaks["hbm_gbs"], "traffic": None,
+                     "frac": bj["gbs"] / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": "of fallback" if peaks.get("fallback") else "of measured (MEASURED_PEAKS.json hbm_gbs)",
                      "ms": bj["ms"], "algorithmic_bytes": bj["bytes"]},
         "jvp_fp64": roof["jvp_fp64"],
+        "probe_tc": roof.get("probe_tc"),
         "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
     if not args.no_serving:
