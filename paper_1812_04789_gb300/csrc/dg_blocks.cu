@@ -334,7 +334,7 @@ static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, size_
     smem = tot * sizeof(T);
     grid = Ms.E;
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(probe_kernel<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      allow_max_smem(probe_kernel<D, T>);
   } else {
     grid = std::min(Ms.E, probe_grid_global());
     if (!scratch || scratch_elems < tot * (size_t)grid) return cudaErrorInvalidValue;
@@ -347,8 +347,9 @@ static cudaError_t run_probe(const Mesh& Ms, const T* W, T sigma, T* Dout, size_
 
 // FP32 blocks go through the tensor-core kernel when the mesh has a plan for
 // it (DG_PROBE_SIMT=1 in the environment selects the SIMT kernel instead); the
-// SIMT kernel then adds only the neighbour-seeded terms: the coarse neighbour
-// blocks, and the faces of a direction with one element (own neighbour).
+// coarse neighbour blocks then come from probe_nbr_kernel, or, when a
+// direction has one element (its faces feed the diagonal block), from the SIMT
+// kernel restricted to the neighbour-seeded terms.
 static bool use_tc(const Mesh& M) {
   const char* e = getenv("DG_PROBE_SIMT");
   return M.tc.ok && M.tc_test && M.tc_trial && !(e && e[0] == '1');
@@ -364,6 +365,7 @@ cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, size_t
     bool self = false;
     for (int k = 0; k < M.d; ++k) self = self || M.desc.n[k] == 1;
     if (O == nullptr && !self) return cudaSuccess;
+    if (!self && probe_nbr_fits(M, nmc)) return launch_probe_nbr(M, (const float*)W, (float*)O, nmc, st);
     nbr_only = true;
   }
   if (M.d == 2) return run_probe<2, T>(M, W, sigma, D, dstride, O, nmc, scratch, scratch_elems, nbr_only, st);

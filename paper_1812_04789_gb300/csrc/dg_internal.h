@@ -13,6 +13,23 @@ namespace dgk {
 
 enum : int { ST_NONPHYSICAL = 1, ST_SINGULAR = 2, ST_NONFINITE = 4, ST_TIMEOUT = 8 };
 
+// Allow a kernel the device's largest dynamic shared memory (the per-block
+// limit less its static shared memory).  Always the same value: host threads that launch one kernel for different meshes at once
+// (serving workers) cannot overwrite each other's setting between setting it
+// and launching.  The actual amount is still given per launch.
+template <class K>
+inline cudaError_t allow_max_smem(K kernel) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  int dev = 0, smax = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the per-block limit covers the kernel's static shared memory too
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smax - (int)fa.sharedSizeBytes);
+}
+
 // host-side count of kernel launches (dg_launch_count)
 unsigned long long& launch_counter();
 inline void note_launch() { __atomic_fetch_add(&launch_counter(), 1ULL, __ATOMIC_RELAXED); }
@@ -89,6 +106,12 @@ size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem);
 cudaError_t launch_probe_tc(const Mesh& M, const float* W, float sigma, float* D, size_t dstride,
                             cudaStream_t st);
 cudaError_t build_tc_tables(Mesh& M);
+
+// FP32 neighbour blocks O[e][2k+side] (first nmc modes per variable, row-major
+// nbc x nbc) for meshes with the tensor-core probe tables and no direction of
+// one element; probe_nbr_fits says whether the kernel applies.
+bool probe_nbr_fits(const Mesh& M, int nmc);
+cudaError_t launch_probe_nbr(const Mesh& M, const float* W, float* O, int nmc, cudaStream_t st);
 
 // Batched in-place inverse of nblk row-major blocks of size nb starting bstride
 // elements apart (bstride >= nb * inv_ld(nb)).  *transposed = 1 when the

@@ -352,7 +352,7 @@ template <class T, int R>
 cudaError_t run_reg(T* A, int nb, size_t bstride, long nblk, int* status, cudaStream_t st) {
   const size_t smem = (size_t)nb * inv_ld<T>(nb) * sizeof(T);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(block_inverse_reg_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(block_inverse_reg_kernel<T, R>);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_inverse_reg_kernel<T, R>, 256, smem);
   const long grid = std::min<long>(nblk, (long)std::max(1, occ) * num_sms_inv());
@@ -387,7 +387,7 @@ cudaError_t launch_block_inverse(T* A, int nb, size_t bstride, long nblk, int* s
   const int use_smem = full <= (size_t)smax - 1024;
   const size_t smem = use_smem ? full : base;
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(block_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(block_inverse_kernel<T>);
   const long grid = std::min<long>(nblk, (use_smem ? 1L : 8L) * num_sms_inv());
   *transposed = use_smem;
   note_launch();

@@ -433,7 +433,7 @@ static cudaError_t run_tc(const Mesh& M, const float* W, float sigma, float* Dou
   int smem = P.smem;
   const int sm_total = 228 * 1024;
   if (per_sm < 8) smem = std::max(smem, sm_total / (per_sm + 1) - 1024 + 16);
-  cudaError_t e = cudaFuncSetAttribute(probe_tc_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = allow_max_smem(probe_tc_kernel<D>);
   if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, probe_tc_kernel<D>, TC_THREADS, smem);

@@ -400,7 +400,7 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
   size_t fsm = face_smem<T>(Ms, fpc, JVP);
   while (fsm > 200 * 1024 && fpc > 1) fsm = face_smem<T>(Ms, --fpc, JVP);
   if (fsm > 48 * 1024)
-    cudaFuncSetAttribute(face_kernel<D, T, JVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    allow_max_smem(face_kernel<D, T, JVP>);
   int nfaces = D * Ms.E;
   note_launch();
   face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc);
@@ -410,8 +410,7 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
     size_t tsm;
     int nqp;
     if (vol_tables_fit(Ms, JVP, &tsm, &nqp)) {
-      cudaFuncSetAttribute(volume_kernel_st<D, JVP, VOL_SLOTS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tsm);
+      allow_max_smem(volume_kernel_st<D, JVP, VOL_SLOTS>);
       int dev = 0, nsm = 1;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -426,7 +425,7 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
   size_t vsm = vol_smem<T>(Ms, epc, JVP);
   while (vsm > 200 * 1024 && epc > 1) vsm = vol_smem<T>(Ms, --epc, JVP);
   if (vsm > 48 * 1024)
-    cudaFuncSetAttribute(volume_kernel<D, T, JVP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+    allow_max_smem(volume_kernel<D, T, JVP>);
   note_launch();
   volume_kernel<D, T, JVP><<<(Ms.E + epc - 1) / epc, 256, vsm, st>>>(mv, ph, W, V, slots, S, sigma, out,
                                                                     Ms.status, epc);
@@ -459,7 +458,7 @@ static cudaError_t run_residual_slots(const Mesh& Ms, const double* W, const dou
   size_t fsm = face_smem<double>(Ms, fpc, false);
   while (fsm > 200 * 1024 && fpc > 1) fsm = face_smem<double>(Ms, --fpc, false);
   if (fsm > 48 * 1024)
-    cudaFuncSetAttribute(face_kernel<D, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+    allow_max_smem(face_kernel<D, double, false>);
   int nfaces = D * Ms.E;
   note_launch();
   face_kernel<D, double, false><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, nullptr, slots,
@@ -470,7 +469,7 @@ static cudaError_t run_residual_slots(const Mesh& Ms, const double* W, const dou
   size_t vsm = vol_smem<double>(Ms, epc, false);
   while (vsm > 200 * 1024 && epc > 1) vsm = vol_smem<double>(Ms, --epc, false);
   if (vsm > 48 * 1024)
-    cudaFuncSetAttribute(volume_kernel<D, double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsm);
+    allow_max_smem(volume_kernel<D, double, false>);
   note_launch();
   volume_kernel<D, double, false><<<(Ms.E + epc - 1) / epc, 256, vsm, st>>>(mv, ph, W, nullptr, slots, S, 0.0,
                                                                            out, Ms.status, epc);

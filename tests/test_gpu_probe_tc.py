@@ -86,3 +86,43 @@ def test_mixed_diag_blocks_vs_oracle(name, kernel, monkeypatch):
     err = np.abs(Dg - D).max() / np.abs(D).max()
     print("%s %s: max |D_gpu - D| / max |D| = %.3e" % (name, kernel, err))
     assert err <= (1e-4 if kernel == "tc" else 2e-6)
+
+
+# neighbour blocks at the first coarse order: (config, sampled elements, coarse p)
+NBR_CASES = {
+    "tgv3d_p2_3x2x4": (CASES["tgv3d_p2_3x2x4"][0], None, 1),
+    "vortex2d_p2_5x7": (CASES["vortex2d_p2_5x7"][0], None, 1),
+    "tgv3d_p4_3x3x3": (CASES["tgv3d_p4_3x3x3"][0], [0, 13, 26], 2),
+    "tgv3d_p5_2x3x2": (CASES["tgv3d_p5_2x3x2"][0], [0, 11], 3),
+}
+
+
+@pytest.mark.parametrize("kernel", ["tc", "simt"])
+@pytest.mark.parametrize("name", list(NBR_CASES))
+def test_mixed_neighbour_blocks_vs_oracle(name, kernel, monkeypatch):
+    """FP32 neighbour blocks dR_e/dW_nbr on the first coarse order (the
+    inherited block-sparse operator's off-diagonal part).  With the tensor-core
+    probe they come from the neighbour-seeded kernel, else from the SIMT probe.
+    Bar 1e-5 relative to max |O|: the same FP32 rounding as the SIMT diagonal
+    blocks, on sums of n_qf (1 + d) K-terms per entry."""
+    if kernel == "simt":
+        monkeypatch.setenv("DG_PROBE_SIMT", "1")
+    else:
+        monkeypatch.delenv("DG_PROBE_SIMT", raising=False)
+    cfg, sample, pc = NBR_CASES[name]
+    om, oph = oracle_mesh(cfg), oracle_physics(cfg)
+    W = wl.perturbed_state(cfg, amp=0.05)
+    elems = np.arange(om.E) if sample is None else np.asarray(sample)
+    O = oblocks.offdiag_blocks(om, oph, W, pc, elems=elems)
+    nbc = om.m * wl.n_modes(pc, om.d)
+    O = O.reshape(len(elems), 2 * om.d, nbc, nbc)
+    m = B.Mesh.from_workload(wl.mesh_desc(cfg), wl.physics(cfg))
+    pmg = B.PMG(m, torch.from_numpy(W).cuda(), 2.5,
+                B.pmg_opts((cfg["p"], pc), nu_pre=2, nu_post=2, nu_coarse=4, precision=B.PREC_MIXED))
+    Og = torch.empty((om.E, 2 * om.d, nbc, nbc), dtype=torch.float32, device="cuda")
+    pmg.export_blocks(1, B.BLOCKS_NEIGHBOUR, Og)
+    assert m.status_sync() == B.DG_OK
+    Og = Og.cpu().numpy().astype(np.float64)[elems]
+    err = np.abs(Og - O).max() / np.abs(O).max()
+    print("%s %s: max |O_gpu - O| / max |O| = %.3e" % (name, kernel, err))
+    assert err <= 1e-5
