@@ -92,7 +92,7 @@ template <class T>
 cudaError_t MG<T>::op(int l, const T* x, T* y, cudaStream_t st) {
   if (l == 0) return launch_residual<T>(*mesh, W, x, nullptr, sigma, true, y, st);
   Level<T>& L = lv[l];
-  return launch_bsr<T>(L.Dop, L.O, mesh->nbr, mesh->d, x, y, L.nb, mesh->E, st);
+  return launch_bsr<T>(L.Dop, L.O, L.cs, L.co_t, mesh->nbr, mesh->d, x, y, L.nb, mesh->E, st);
 }
 
 // SMOOTH / SOLVE: nu iterations of GMRES right-preconditioned by block Jacobi,
@@ -192,8 +192,17 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
     L.bs = (size_t)L.nb * inv_ld<T>(L.nb);
     CK(dalloc(mg.allocs, (void**)&L.Dinv, sizeof(T) * (size_t)M.E * L.bs, &h->block_bytes));
     if (l >= 1) {
-      CK(dalloc(mg.allocs, (void**)&L.Dop, sizeof(T) * nbl, &h->block_bytes));
-      CK(dalloc(mg.allocs, (void**)&L.O, sizeof(T) * nbl * 2 * M.d, &h->block_bytes));
+      // coarse blocks column-major when the FP32 neighbour blocks come from
+      // probe_nbr_kernel (decided here once: the captured graph relies on it)
+      // (the column-major mat-vec runs one thread per block and 16 bytes of rows: at most 256 per element)
+      const int tpb1 = (1 + 2 * M.d) * (inv_ld<T>(mg.lv[1].nb) / (int)(16 / sizeof(T)));
+      L.co_t = std::is_same<T, float>::value && tpb1 <= 256 && probe_nbr_colmajor_ok(M, mg.lv[1].nm) ? 1 : 0;
+      L.cs = L.co_t ? L.bs : (size_t)L.nb * L.nb;
+      (void)nbl;
+      CK(dalloc(mg.allocs, (void**)&L.Dop, sizeof(T) * (size_t)M.E * L.cs, &h->block_bytes));
+      CK(dalloc(mg.allocs, (void**)&L.O, sizeof(T) * (size_t)M.E * 2 * M.d * L.cs, &h->block_bytes));
+      CK(cudaMemset(L.Dop, 0, sizeof(T) * (size_t)M.E * L.cs));   // padding rows stay zero
+      CK(cudaMemset(L.O, 0, sizeof(T) * (size_t)M.E * 2 * M.d * L.cs));
     }
     for (T** v : {&L.x, &L.b, &L.r, &L.t}) CK(dalloc(mg.allocs, (void**)v, sizeof(T) * L.N, &h->vector_bytes));
     int nmax = (l == nl - 1) ? std::max(1, o.nu_coarse) : std::max(std::max(L.nu_pre, L.nu_post), 1);
@@ -229,15 +238,18 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
   else
     CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
   CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, mg.lv[0].bs, nl > 1 ? mg.lv[1].O : nullptr,
-                            nl > 1 ? mg.lv[1].nm : 0, mg.scratch, mg.scratch_elems, st));
+                            nl > 1 ? mg.lv[1].nm : 0, nl > 1 ? mg.lv[1].co_t : 0, mg.scratch, mg.scratch_elems,
+                            st));
+  const Level<T>& F = mg.lv[0];
   for (int l = 1; l < nl; ++l) {
     Level<T>& L = mg.lv[l];
-    CK(launch_truncate_blocks<T>(mg.lv[0].Dinv, mg.lv[0].nm, mg.lv[0].bs, L.Dop, L.nm, M.m, M.E, st));
+    // inherited diagonal blocks: for the operator (layout of the level) and,
+    // row-major, as the input of the inverse
+    CK(launch_truncate_blocks<T>(F.Dinv, F.nm, F.bs, 0, L.Dop, L.nm, L.cs, L.co_t, M.m, M.E, st));
+    CK(launch_truncate_blocks<T>(F.Dinv, F.nm, F.bs, 0, L.Dinv, L.nm, L.bs, 0, M.m, M.E, st));
     if (l >= 2)
-      CK(launch_truncate_blocks<T>(mg.lv[1].O, mg.lv[1].nm, (size_t)mg.lv[1].nb * mg.lv[1].nb, L.O, L.nm, M.m,
-                                   (long)M.E * 2 * M.d, st));
-    CK(cudaMemcpy2DAsync(L.Dinv, sizeof(T) * L.bs, L.Dop, sizeof(T) * L.nb * L.nb, sizeof(T) * L.nb * L.nb, M.E,
-                         cudaMemcpyDeviceToDevice, st));
+      CK(launch_truncate_blocks<T>(mg.lv[1].O, mg.lv[1].nm, mg.lv[1].cs, mg.lv[1].co_t, L.O, L.nm, L.cs, L.co_t,
+                                   M.m, (long)M.E * 2 * M.d, st));
   }
   for (int l = 0; l < nl; ++l)
     CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, mg.lv[l].bs, M.E, M.status, &mg.lv[l].inv_t, st));
@@ -454,58 +466,42 @@ extern "C" dg_status dg_pmg_bytes(dg_pmg h, size_t* block_bytes, size_t* vector_
   return DG_OK;
 }
 
+// Row-major packed copy of a level's blocks (any storage layout).
+template <class T>
+static dg_status export_level(const MG<T>& mg, const Mesh& M, T* W, double sigma, int level, int which, T* out,
+                              size_t out_bytes, cudaStream_t st) {
+  const Level<T>& L = mg.lv[level];
+  const int nb = L.nb;
+  const size_t nblk = which == DG_BLOCKS_NEIGHBOUR ? (size_t)M.E * 2 * M.d : (size_t)M.E;
+  if (out_bytes < nblk * nb * nb * sizeof(T)) return DG_ERR_INVALID;
+  if (which == DG_BLOCKS_DIAG_INV) {
+    CK(launch_unpack_inverse<T>(L.Dinv, L.bs, L.inv_t, out, nb, (long)nblk, st));
+  } else if (which == DG_BLOCKS_NEIGHBOUR) {
+    if (level < 1) return DG_ERR_INVALID;
+    CK(launch_unpack_inverse<T>(L.O, L.cs, L.co_t, out, nb, (long)nblk, st));
+  } else if (which == DG_BLOCKS_DIAG) {
+    if (level == 0)   // the fine-level probe again, at the stored state and shift
+      CK(launch_probe_blocks<T>(M, W, (T)sigma, out, (size_t)nb * nb, nullptr, 0, 0, mg.scratch, mg.scratch_elems,
+                                st));
+    else
+      CK(launch_unpack_inverse<T>(L.Dop, L.cs, L.co_t, out, nb, (long)nblk, st));
+  } else {
+    return DG_ERR_INVALID;
+  }
+  CK(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
 extern "C" dg_status dg_pmg_export_blocks(dg_pmg h, int level, int which, void* out, size_t out_bytes,
                                           void* stream) {
   if (!h || !out) return DG_ERR_INVALID;
   const Mesh& M = h->mesh->m;
   int nl = (int)(h->precision == DG_PREC_FP64 ? h->mg64.lv.size() : h->mg32.lv.size());
   if (level < 0 || level >= nl) return DG_ERR_INVALID;
-  size_t es = h->precision == DG_PREC_FP64 ? sizeof(double) : sizeof(float);
-  int nb = h->precision == DG_PREC_FP64 ? h->mg64.lv[level].nb : h->mg32.lv[level].nb;
-  const void* src;
-  size_t cnt;
-  if (which == DG_BLOCKS_DIAG_INV) {   // unpacked to row-major nb x nb blocks
-    cnt = (size_t)M.E * nb * nb;
-    if (out_bytes < cnt * es) return DG_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (h->precision == DG_PREC_FP64) {
-      const Level<double>& L = h->mg64.lv[level];
-      CK(launch_unpack_inverse<double>(L.Dinv, L.bs, L.inv_t, (double*)out, nb, M.E, st));
-    } else {
-      const Level<float>& L = h->mg32.lv[level];
-      CK(launch_unpack_inverse<float>(L.Dinv, L.bs, L.inv_t, (float*)out, nb, M.E, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    return DG_OK;
-  } else if (which == DG_BLOCKS_NEIGHBOUR) {
-    if (level < 1) return DG_ERR_INVALID;
-    src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].O : (const void*)h->mg32.lv[level].O;
-    cnt = (size_t)M.E * 2 * M.d * nb * nb;
-  } else if (which == DG_BLOCKS_DIAG) {
-    cnt = (size_t)M.E * nb * nb;
-    if (out_bytes < cnt * es) return DG_ERR_INVALID;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (level == 0) {   // the fine-level probe again, at the stored state and shift
-      if (h->precision == DG_PREC_FP64)
-        CK(launch_probe_blocks<double>(M, h->mg64.W, h->sigma, (double*)out, (size_t)nb * nb, nullptr, 0,
-                                       h->mg64.scratch, h->mg64.scratch_elems, st));
-      else
-        CK(launch_probe_blocks<float>(M, h->mg32.W, (float)h->sigma, (float*)out, (size_t)nb * nb, nullptr, 0,
-                                      h->mg32.scratch, h->mg32.scratch_elems, st));
-    } else {
-      src = h->precision == DG_PREC_FP64 ? (const void*)h->mg64.lv[level].Dop : (const void*)h->mg32.lv[level].Dop;
-      CK(cudaMemcpyAsync(out, src, cnt * es, cudaMemcpyDeviceToDevice, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    return DG_OK;
-  } else {
-    return DG_ERR_INVALID;
-  }
-  if (out_bytes < cnt * es) return DG_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
-  CK(cudaMemcpyAsync(out, src, cnt * es, cudaMemcpyDeviceToDevice, st));
-  CK(cudaStreamSynchronize(st));
-  return DG_OK;
+  if (h->precision == DG_PREC_FP64)
+    return export_level<double>(h->mg64, M, h->mg64.W, h->sigma, level, which, (double*)out, out_bytes, st);
+  return export_level<float>(h->mg32, M, h->mg32.W, h->sigma, level, which, (float*)out, out_bytes, st);
 }
 
 extern "C" dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, const double* b, double sigma,

@@ -357,7 +357,15 @@ static bool use_tc(const Mesh& M) {
 
 template <class T>
 cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, size_t dstride, T* O, int nmc,
-                                T* scratch, size_t scratch_elems, cudaStream_t st) {
+                                int nbr_colmajor, T* scratch, size_t scratch_elems, cudaStream_t st) {
+  if (std::is_same<T, float>::value && nbr_colmajor && O) {
+    // layout fixed at setup: the neighbour blocks always come from probe_nbr_kernel
+    cudaError_t e = use_tc(M) ? launch_probe_tc(M, (const float*)W, (float)sigma, (float*)D, dstride, st)
+                   : M.d == 2 ? run_probe<2, T>(M, W, sigma, D, dstride, nullptr, 0, scratch, scratch_elems, false, st)
+                              : run_probe<3, T>(M, W, sigma, D, dstride, nullptr, 0, scratch, scratch_elems, false, st);
+    if (e != cudaSuccess) return e;
+    return launch_probe_nbr(M, (const float*)W, (float*)O, nmc, 1, st);
+  }
   bool nbr_only = false;
   if (std::is_same<T, float>::value && use_tc(M)) {
     cudaError_t e = launch_probe_tc(M, (const float*)W, (float)sigma, (float*)D, dstride, st);
@@ -365,45 +373,52 @@ cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, size_t
     bool self = false;
     for (int k = 0; k < M.d; ++k) self = self || M.desc.n[k] == 1;
     if (O == nullptr && !self) return cudaSuccess;
-    if (!self && probe_nbr_fits(M, nmc)) return launch_probe_nbr(M, (const float*)W, (float*)O, nmc, st);
+    if (!self && probe_nbr_fits(M, nmc)) return launch_probe_nbr(M, (const float*)W, (float*)O, nmc, 0, st);
     nbr_only = true;
   }
   if (M.d == 2) return run_probe<2, T>(M, W, sigma, D, dstride, O, nmc, scratch, scratch_elems, nbr_only, st);
   return run_probe<3, T>(M, W, sigma, D, dstride, O, nmc, scratch, scratch_elems, nbr_only, st);
 }
 template cudaError_t launch_probe_blocks<double>(const Mesh&, const double*, double, double*, size_t, double*,
-                                                 int, double*, size_t, cudaStream_t);
+                                                 int, int, double*, size_t, cudaStream_t);
 template cudaError_t launch_probe_blocks<float>(const Mesh&, const float*, float, float*, size_t, float*, int,
-                                                float*, size_t, cudaStream_t);
+                                                int, float*, size_t, cudaStream_t);
+
+bool probe_nbr_colmajor_ok(const Mesh& M, int nmc) { return use_tc(M) && probe_nbr_fits(M, nmc); }
 
 // ---------------------------------------------------------------- truncation
 template <class T>
-__global__ void truncate_kernel(const T* __restrict__ src, int nms, size_t sstride, T* __restrict__ dst,
-                                int nmt, int m, long nblk) {
-  const int nbs = m * nms, nbt = m * nmt;
+__global__ void truncate_kernel(const T* __restrict__ src, int nms, size_t sstride, int src_t, T* __restrict__ dst,
+                                int nmt, size_t dstride, int dst_t, int m, long nblk) {
+  const int nbs = m * nms, nbt = m * nmt, lds = inv_ld<T>(nbs), ldt = inv_ld<T>(nbt);
   const long tot = nblk * nbt * nbt;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
-    long b = t / ((long)nbt * nbt);
-    int r = (int)(t % ((long)nbt * nbt));
-    int row = r / nbt, col = r % nbt;
-    int v = row / nmt, i = row % nmt, w = col / nmt, j = col % nmt;
-    dst[t] = src[(size_t)b * sstride + (size_t)(v * nms + i) * nbs + (w * nms + j)];
+    const long b = t / ((long)nbt * nbt);
+    const int r = (int)(t % ((long)nbt * nbt));
+    // consecutive t walk the destination's contiguous dimension
+    const int a1 = r / nbt, a2 = r % nbt;
+    const int row = dst_t ? a2 : a1, col = dst_t ? a1 : a2;
+    const int v = row / nmt, i = row % nmt, w = col / nmt, j = col % nmt;
+    const int rs = v * nms + i, cs = w * nms + j;
+    const T x = src[(size_t)b * sstride + (src_t ? (size_t)cs * lds + rs : (size_t)rs * nbs + cs)];
+    dst[(size_t)b * dstride + (dst_t ? (size_t)col * ldt + row : (size_t)row * nbt + col)] = x;
   }
 }
 
 template <class T>
-cudaError_t launch_truncate_blocks(const T* src, int nms, size_t sstride, T* dst, int nmt, int m, long nblk,
-                                   cudaStream_t st) {
+cudaError_t launch_truncate_blocks(const T* src, int nms, size_t sstride, int src_t, T* dst, int nmt,
+                                   size_t dstride, int dst_t, int m, long nblk, cudaStream_t st) {
   long tot = nblk * (long)(m * nmt) * (m * nmt);
   if (tot <= 0) return cudaSuccess;
   long grid = std::min<long>((tot + 255) / 256, 65535L * 8);
   note_launch();
-  truncate_kernel<T><<<(int)grid, 256, 0, st>>>(src, nms, sstride, dst, nmt, m, nblk);
+  truncate_kernel<T><<<(int)grid, 256, 0, st>>>(src, nms, sstride, src_t, dst, nmt, dstride, dst_t, m, nblk);
   return cudaGetLastError();
 }
-template cudaError_t launch_truncate_blocks<double>(const double*, int, size_t, double*, int, int, long,
-                                                    cudaStream_t);
-template cudaError_t launch_truncate_blocks<float>(const float*, int, size_t, float*, int, int, long, cudaStream_t);
+template cudaError_t launch_truncate_blocks<double>(const double*, int, size_t, int, double*, int, size_t, int, int,
+                                                    long, cudaStream_t);
+template cudaError_t launch_truncate_blocks<float>(const float*, int, size_t, int, float*, int, size_t, int, int,
+                                                   long, cudaStream_t);
 
 // ---------------------------------------------------------------- block apply / BSR
 // One CTA per element: the element's input (and neighbours' for BSR) staged in
@@ -443,7 +458,7 @@ __global__ void __launch_bounds__(256) bsr_kernel(const T* __restrict__ Dm, size
                   lane, s0, s1);
       if (O) {
         for (int s = 0; s < nf; ++s) {
-          const T* Ob = O + ((size_t)e * nf + s) * nb * nb;
+          const T* Ob = O + ((size_t)e * nf + s) * dstride;
           row_dot2<T>(Ob + (size_t)r0 * nb, Ob + (size_t)r1 * nb, xs + (size_t)(1 + s) * nb, nb, lane, s0, s1);
         }
       }
@@ -567,18 +582,88 @@ cudaError_t launch_unpack_inverse(const T* A, size_t bstride, int transposed, T*
 template cudaError_t launch_unpack_inverse<double>(const double*, size_t, int, double*, int, long, cudaStream_t);
 template cudaError_t launch_unpack_inverse<float>(const float*, size_t, int, float*, int, long, cudaStream_t);
 
+// Block-sparse mat-vec on column-major blocks (leading dimension ld =
+// inv_ld(nb)): y_e = D_e x_e + sum_s O_{e,s} x_nbr(e,s).  A thread owns one
+// block b of one element and 16 bytes of its rows and streams the block's
+// columns with one vector load each (so an element keeps (1 + 2d) ld / 4 FP32
+// threads busy); the element's and its neighbours' inputs are staged in shared
+// memory and the per-block partial rows are summed in a fixed order.
 template <class T>
-cudaError_t launch_bsr(const T* D, const T* O, const int* nbr, int d, const T* x, T* y, int nb, int E,
-                       cudaStream_t st) {
+__global__ void __launch_bounds__(256) bsr_colmajor_kernel(const T* __restrict__ Dm, const T* __restrict__ O,
+                                                           size_t bstride, const int* __restrict__ nbr, int nf,
+                                                           const T* __restrict__ x, T* __restrict__ y, int nb,
+                                                           int ld, int E, int epc, int tpe) {
+  constexpr int R = Vec16<T>::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nsrc = 1 + nf, tpb = nsrc * tpe;
+  T* xs = reinterpret_cast<T*>(smem_raw);           // [epc][nsrc][nb]
+  T* part = xs + (size_t)epc * nsrc * nb;           // [epc][nsrc][ld]
+  const int sub = threadIdx.x / tpb, r = threadIdx.x - sub * tpb, b = r / tpe, tt = r - b * tpe;
+  for (long e0 = (long)blockIdx.x * epc; e0 < E; e0 += (long)gridDim.x * epc) {
+    const int nl = (int)min((long)epc, E - e0);
+    for (int t = threadIdx.x; t < nl * nsrc * nb; t += blockDim.x) {
+      const int el = t / (nsrc * nb), q = t - el * nsrc * nb, who = q / nb, j = q - who * nb;
+      const long e = e0 + el;
+      const long src = who == 0 ? e : nbr[(size_t)e * nf + who - 1];
+      xs[t] = x[(size_t)src * nb + j];
+    }
+    __syncthreads();
+    if (sub < nl) {
+      const long e = e0 + sub;
+      const T* base = (b == 0 ? Dm + (size_t)e * bstride : O + ((size_t)e * nf + b - 1) * bstride) + R * tt;
+      const T* xb = xs + ((size_t)sub * nsrc + b) * nb;
+      T acc[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[j] = T(0);
+#pragma unroll 8
+      for (int c = 0; c < nb; ++c) {
+        T a[R];
+        Vec16<T>::load(base + (size_t)c * ld, a);
+        const T xv = xb[c];
+#pragma unroll
+        for (int j = 0; j < R; ++j) acc[j] += a[j] * xv;
+      }
+      T* pr = part + ((size_t)sub * nsrc + b) * ld + R * tt;
+#pragma unroll
+      for (int j = 0; j < R; ++j) pr[j] = acc[j];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) {
+      const int el = t / nb, row = t - el * nb;
+      const T* pe = part + (size_t)el * nsrc * ld + row;
+      T sum = T(0);
+      for (int bb = 0; bb < nsrc; ++bb) sum += pe[(size_t)bb * ld];
+      y[(size_t)(e0 + el) * nb + row] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+cudaError_t launch_bsr(const T* D, const T* O, size_t bstride, int transposed, const int* nbr, int d, const T* x,
+                       T* y, int nb, int E, cudaStream_t st) {
+  if (transposed) {
+    const int ld = inv_ld<T>(nb), tpe = ld / Vec16<T>::N, tpb = (1 + 2 * d) * tpe;
+    if (tpb <= 256) {
+      const int epc = std::max(1, 256 / tpb);
+      const int threads = (epc * tpb + 31) / 32 * 32;
+      const int grid = std::min((E + epc - 1) / epc, 16 * num_sms());
+      const size_t smem = (size_t)epc * (1 + 2 * d) * (nb + ld) * sizeof(T);
+      note_launch();
+      bsr_colmajor_kernel<T><<<grid, threads, smem, st>>>(D, O, bstride, nbr, 2 * d, x, y, nb, ld, E, epc, tpe);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;   // coarse blocks this large are stored row-major
+  }
   int grid = std::min(E, 32 * num_sms());
   size_t smem = (size_t)(1 + 2 * d) * nb * sizeof(T);
   note_launch();
-  bsr_kernel<T><<<grid, 256, smem, st>>>(D, (size_t)nb * nb, O, nbr, 2 * d, x, y, nb, E);
+  bsr_kernel<T><<<grid, 256, smem, st>>>(D, bstride, O, nbr, 2 * d, x, y, nb, E);
   return cudaGetLastError();
 }
-template cudaError_t launch_bsr<double>(const double*, const double*, const int*, int, const double*, double*,
-                                        int, int, cudaStream_t);
-template cudaError_t launch_bsr<float>(const float*, const float*, const int*, int, const float*, float*, int,
-                                       int, cudaStream_t);
+template cudaError_t launch_bsr<double>(const double*, const double*, size_t, int, const int*, int, const double*,
+                                        double*, int, int, cudaStream_t);
+template cudaError_t launch_bsr<float>(const float*, const float*, size_t, int, const int*, int, const float*,
+                                       float*, int, int, cudaStream_t);
 
 }  // namespace dgk

@@ -93,10 +93,12 @@ cudaError_t launch_residual_with_slots(const Mesh& M, const double* W, const dou
 // Element Jacobian blocks by probing: D[e] = dR_e/dW_e + sigma |J| I (nb x nb),
 // and when O != nullptr the neighbour blocks O[e][2k+side] restricted to the
 // first nmc modes of every variable (nbc x nbc, nbc = m nmc).
-// D[e] starts at D + e * dstride (row-major, row stride nb).
+// D[e] starts at D + e * dstride (row-major, row stride nb).  With
+// nbr_colmajor (FP32 only, probe_nbr_colmajor_ok) the neighbour blocks are
+// written column-major by probe_nbr_kernel, else row-major, nbc^2 apart.
 template <class T>
 cudaError_t launch_probe_blocks(const Mesh& M, const T* W, T sigma, T* D, size_t dstride, T* O, int nmc,
-                                T* scratch, size_t scratch_elems, cudaStream_t st);
+                                int nbr_colmajor, T* scratch, size_t scratch_elems, cudaStream_t st);
 template <class T>
 size_t probe_scratch_elems(const Mesh& M, int nmc, bool* fits_smem);
 
@@ -110,8 +112,13 @@ cudaError_t build_tc_tables(Mesh& M);
 // FP32 neighbour blocks O[e][2k+side] (first nmc modes per variable, row-major
 // nbc x nbc) for meshes with the tensor-core probe tables and no direction of
 // one element; probe_nbr_fits says whether the kernel applies.
+// colmajor: blocks column-major with leading dimension inv_ld(nbc), nbc *
+// inv_ld(nbc) apart (else row-major, nbc^2 apart).
 bool probe_nbr_fits(const Mesh& M, int nmc);
-cudaError_t launch_probe_nbr(const Mesh& M, const float* W, float* O, int nmc, cudaStream_t st);
+cudaError_t launch_probe_nbr(const Mesh& M, const float* W, float* O, int nmc, int colmajor, cudaStream_t st);
+// Whether the FP32 neighbour blocks of this mesh come from probe_nbr_kernel
+// (tensor-core tables present, the kernel applies, not disabled by DG_PROBE_SIMT).
+bool probe_nbr_colmajor_ok(const Mesh& M, int nmc);
 
 // Batched in-place inverse of nblk row-major blocks of size nb starting bstride
 // elements apart (bstride >= nb * inv_ld(nb)).  *transposed = 1 when the
@@ -128,10 +135,11 @@ cudaError_t launch_block_inverse(T* A, int nb, size_t bstride, long nblk, int* s
                                  cudaStream_t st);
 
 // Leading sub-block per variable pair: dst[b] (m nmt)^2 from src[b] (m nms)^2.
-// Source blocks start sstride elements apart (row-major, row stride m nms).
+// Blocks start sstride / dstride elements apart; *_t = 1: column-major with
+// leading dimension inv_ld(nb), 0: row-major (row stride nb).
 template <class T>
-cudaError_t launch_truncate_blocks(const T* src, int nms, size_t sstride, T* dst, int nmt, int m, long nblk,
-                                   cudaStream_t st);
+cudaError_t launch_truncate_blocks(const T* src, int nms, size_t sstride, int src_t, T* dst, int nmt,
+                                   size_t dstride, int dst_t, int m, long nblk, cudaStream_t st);
 
 // z[e] = Ainv[e] r[e]; blocks bstride apart, column-major with leading
 // dimension inv_ld(nb) when transposed, else row-major.
@@ -144,10 +152,11 @@ template <class T>
 cudaError_t launch_unpack_inverse(const T* A, size_t bstride, int transposed, T* out, int nb, long nblk,
                                   cudaStream_t st);
 
-// y = D x + sum_s O_s x_nbr(s)
+// y = D x + sum_s O_s x_nbr(s); blocks bstride apart (D: [E], O: [E][2d]),
+// column-major with leading dimension inv_ld(nb) when transposed.
 template <class T>
-cudaError_t launch_bsr(const T* D, const T* O, const int* nbr, int d, const T* x, T* y, int nb,
-                       int E, cudaStream_t st);
+cudaError_t launch_bsr(const T* D, const T* O, size_t bstride, int transposed, const int* nbr, int d,
+                       const T* x, T* y, int nb, int E, cudaStream_t st);
 
 // vector helpers
 template <class T> cudaError_t launch_axpby(long n, double a, const T* x, double b, T* y, cudaStream_t st);
@@ -199,7 +208,9 @@ struct Level {
   size_t bs = 0;             // block stride of Dinv: nb * inv_ld<T>(nb)
   int inv_t = 0;             // Dinv column-major (1) or row-major (0)
   T* Dop = nullptr;          // diagonal blocks of the inherited operator (l >= 1)
-  T* O = nullptr;            // neighbour blocks [E][2d][nb][nb] (l >= 1)
+  T* O = nullptr;            // neighbour blocks [E][2d] (l >= 1)
+  int co_t = 0;              // Dop and O column-major (1, leading dimension inv_ld(nb)) or row-major
+  size_t cs = 0;             // block stride of Dop and O
   T *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   int nu_pre = 0, nu_post = 0;
   Krylov<T> kr;

@@ -62,7 +62,7 @@ NbrPlan nbr_plan(int d, int nm, int nqf, int nmc, int smax) {
 template <int D>
 __global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> mv, Phys<float> ph,
                                                                 const float* __restrict__ W,
-                                                                float* __restrict__ Oout, int nmc,
+                                                                float* __restrict__ Oout, int nmc, int ldo,
                                                                 const float* __restrict__ test, int npv,
                                                                 int nmp, NbrPlan P, int* status) {
   using T = float;
@@ -77,13 +77,16 @@ __global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> 
   T* Zs = sm + P.oZ;   // [jq][row][4], row = (w, v, i')
   const int nm = mv.nm, nqf = mv.nqf, E = mv.E, jq = P.jq;
   const int R = M * M * nmc, nbc = M * nmc;
+  // ldo > 0: blocks column-major with leading dimension ldo, nbc * ldo apart;
+  // ldo == 0: row-major, nbc * nbc apart
+  const size_t ostride = ldo > 0 ? (size_t)nbc * ldo : (size_t)nbc * nbc;
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
     int nbrs[NF];
 #pragma unroll
     for (int s = 0; s < NF; ++s) nbrs[s] = mv.nbr[e * NF + s];
     probe_stage_primal<D, T>(mv, ph, W, e, nbrs, cW, nullptr, cFU, false, status);
     for (int s = 0; s < NF; ++s) {
-      T* Os = Oout + ((size_t)e * NF + s) * nbc * nbc;
+      T* Os = Oout + ((size_t)e * NF + s) * ostride;
       const int f = s ^ 1;   // the neighbour's local face
       for (int q0 = 0; q0 < nqf; q0 += jq) {
         const int ncj = min(jq, nqf - q0);
@@ -159,7 +162,8 @@ __global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> 
 #pragma unroll
             for (int sd = 0; sd < 4; ++sd) acc += z[sd] * tn[sd * nmc];
           }
-          T* o = Os + (size_t)(v * nmc + ip) * nbc + w * nmc + i;
+          T* o = ldo > 0 ? Os + (size_t)(w * nmc + i) * ldo + v * nmc + ip
+                         : Os + (size_t)(v * nmc + ip) * nbc + w * nmc + i;
           *o = q0 == 0 ? acc : *o + acc;
         }
         __syncthreads();
@@ -187,7 +191,8 @@ bool probe_nbr_fits(const Mesh& M, int nmc) {
   return nbr_plan(M.d, M.nm, M.nqf, nmc, smax).ok != 0;
 }
 
-cudaError_t launch_probe_nbr(const Mesh& M, const float* W, float* O, int nmc, cudaStream_t st) {
+cudaError_t launch_probe_nbr(const Mesh& M, const float* W, float* O, int nmc, int colmajor, cudaStream_t st) {
+  const int ldo = colmajor ? inv_ld<float>((M.d + 2) * nmc) : 0;
   int dev = 0, smax = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -209,10 +214,10 @@ cudaError_t launch_probe_nbr(const Mesh& M, const float* W, float* O, int nmc, c
   const int grid = std::min(M.E, std::max(1, occ) * num_sms_nbr());
   note_launch();
   if (M.d == 2)
-    probe_nbr_kernel<2><<<grid, NBR_THREADS, P.smem, st>>>(M.view<float>(), M.phys_t<float>(), W, O, nmc,
+    probe_nbr_kernel<2><<<grid, NBR_THREADS, P.smem, st>>>(M.view<float>(), M.phys_t<float>(), W, O, nmc, ldo,
                                                            M.tc_test, M.tc.npv, M.tc.nmp, P, M.status);
   else
-    probe_nbr_kernel<3><<<grid, NBR_THREADS, P.smem, st>>>(M.view<float>(), M.phys_t<float>(), W, O, nmc,
+    probe_nbr_kernel<3><<<grid, NBR_THREADS, P.smem, st>>>(M.view<float>(), M.phys_t<float>(), W, O, nmc, ldo,
                                                            M.tc_test, M.tc.npv, M.tc.nmp, P, M.status);
   return cudaGetLastError();
 }

@@ -97,7 +97,7 @@ size_t estimate_bytes(const Key& k) {
   for (int l = 0; l < nl; ++l) {
     long nb = m * nmodes(k.opts.p_level[l]);
     const long ld = (nb + (long)(16 / es) - 1) / (long)(16 / es) * (long)(16 / es);   // padded inverse rows
-    bytes += (size_t)E * nb * ld * es + (l == 0 ? 0 : (size_t)E * nb * nb * es * (1 + 2 * d.dim));
+    bytes += (size_t)E * nb * ld * es * (l == 0 ? 1 : 2 + 2 * d.dim);   // inverse (+ coarse D and O)
     int nu = l == nl - 1 ? k.opts.nu_coarse : std::max(k.opts.nu_pre[l], k.opts.nu_post[l]);
     bytes += (size_t)E * nb * es * (2 * nu + 8);
   }
