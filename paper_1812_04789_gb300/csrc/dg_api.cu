@@ -90,7 +90,7 @@ static cudaError_t fd_jvp(const Mesh& M, const double* W, const double* RW, doub
 // ---------------------------------------------------------------- multigrid
 template <class T>
 cudaError_t MG<T>::op(int l, const T* x, T* y, cudaStream_t st) {
-  if (l == 0) return launch_residual<T>(*mesh, W, x, nullptr, sigma, true, y, st);
+  if (l == 0) return launch_residual<T>(*mesh, W, x, nullptr, sigma, true, y, st, Pv, Pf);
   Level<T>& L = lv[l];
   return launch_bsr<T>(L.Dop, L.O, L.cs, L.co_t, mesh->nbr, mesh->d, x, y, L.nb, mesh->E, st);
 }
@@ -211,6 +211,14 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
       h->vector_bytes += L.kr.bytes();
     }
   }
+  // primal traces of the fine JVP's linearisation point (FP32 smoother JVPs);
+  // DG_PMG_NO_PRIMAL_CACHE=1 makes every JVP interpolate W itself
+  const char* npc = getenv("DG_PMG_NO_PRIMAL_CACHE");
+  if (std::is_same<T, float>::value && !(npc && npc[0] == '1') && o.cycle != DG_CYCLE_BJ) {
+    size_t nf = 0, nv = primal_cache_sizes(M, &nf);
+    CK(dalloc(mg.allocs, (void**)&mg.Pv, sizeof(T) * nv, &h->vector_bytes));
+    CK(dalloc(mg.allocs, (void**)&mg.Pf, sizeof(T) * nf, &h->vector_bytes));
+  }
   // probing caches live in global memory when they exceed shared memory
   bool fits = true;
   size_t tot = probe_scratch_elems<T>(M, nl > 1 ? mg.lv[1].nm : 0, &fits);
@@ -237,6 +245,7 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
     CK(cudaMemcpyAsync(mg.W, W64, sizeof(double) * N0, cudaMemcpyDeviceToDevice, st));
   else
     CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
+  if (mg.Pv) CK(launch_primal_cache(M, (const float*)mg.W, (float*)mg.Pv, (float*)mg.Pf, st));
   CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, mg.lv[0].bs, nl > 1 ? mg.lv[1].O : nullptr,
                             nl > 1 ? mg.lv[1].nm : 0, nl > 1 ? mg.lv[1].co_t : 0, mg.scratch, mg.scratch_elems,
                             st));

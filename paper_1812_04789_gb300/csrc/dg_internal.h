@@ -81,9 +81,17 @@ struct Mesh {
 // ----------------------------------------------------------------- kernels
 // Residual (jvp = false) or exact JVP (jvp = true) in precision T:
 // out = [R(W) - S] or [sigma |J| V + dR/dW(W) V].
+// For a JVP, Pv / Pf (optional, FP32 only) hold the primal traces of W from
+// launch_primal_cache: the kernels then interpolate only V.
 template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
-                            T* out, cudaStream_t st);
+                            T* out, cudaStream_t st, const T* Pv = nullptr, const T* Pf = nullptr);
+
+// Primal traces (u, grad u) of an FP32 state at the volume points and on both
+// sides of every face point; primal_cache_sizes returns the volume cache's
+// length and sets the face cache's (floats).
+size_t primal_cache_sizes(const Mesh& M, size_t* nface);
+cudaError_t launch_primal_cache(const Mesh& M, const float* W, float* Pv, float* Pf, cudaStream_t st);
 
 // FP64 residual writing its face terms to `slots` (E * d * 2 * nb doubles)
 // instead of the mesh handle's face-slot workspace.
@@ -226,6 +234,8 @@ struct MG {
   int cycle = 0;
   T* scratch = nullptr;      // probing caches in global memory (large blocks only)
   size_t scratch_elems = 0;
+  T* Pv = nullptr;           // primal traces of W for the fine JVPs (mixed precision;
+  T* Pf = nullptr;           //   refreshed with the blocks), else null
   std::vector<void*> allocs;
   cudaError_t op(int l, const T* x, T* y, cudaStream_t st);
   cudaError_t smooth(int l, const T* b, T* x, int nu, cudaStream_t st);

@@ -33,9 +33,10 @@ template <int D, class T, bool JVP>
 __global__ void __launch_bounds__(128) face_kernel(MeshView<T> mv, Phys<T> ph,
                                                    const T* __restrict__ W,
                                                    const T* __restrict__ V,
-                                                   T* __restrict__ slots, int* status, int fpc) {
+                                                   T* __restrict__ slots, int* status, int fpc,
+                                                   const T* __restrict__ Pf) {
   using S = typename std::conditional<JVP, Dual<T>, T>::type;
-  constexpr int M = D + 2;
+  constexpr int M = D + 2, PU = M * (1 + D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int nb = mv.nb, nm = mv.nm, nqf = mv.nqf, E = mv.E;
@@ -54,11 +55,12 @@ __global__ void __launch_bounds__(128) face_kernel(MeshView<T> mv, Phys<T> ph,
     int fl = t / (2 * nb), r = t % (2 * nb), side = r / nb, j = r % nb;
     int f = f0 + fl, k = f / E, e = f % E;
     int el = side == 0 ? e : mv.nbr[(e * D + k) * 2 + 1];
-    sW[t] = W[(size_t)el * nb + j];
+    if (!Pf) sW[t] = W[(size_t)el * nb + j];
     if (JVP) sV[t] = V[(size_t)el * nb + j];
   }
   __syncthreads();
-  // phase 1: pointwise physics at the face points
+  // phase 1: pointwise physics at the face points (with Pf, a JVP takes the
+  // primal traces of both sides from the cache and interpolates only v)
   for (int t = threadIdx.x; t < nloc * nqf; t += blockDim.x) {
     int fl = t / nqf, q = t % nqf;
     int f = f0 + fl, k = f / E;
@@ -78,7 +80,53 @@ __global__ void __launch_bounds__(128) face_kernel(MeshView<T> mv, Phys<T> ph,
     const T* wR = wL + nb;
     const T* vL = sV + (size_t)fl * 2 * nb;
     const T* vR = vL + nb;
-    for (int i = 0; i < nm; ++i) {
+    bool interp = true;
+    if constexpr (JVP) {
+      if (Pf) {
+        interp = false;
+        T tL[M], tR[M], hL[M][D], hR[M][D];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          tL[v] = tR[v] = T(0);
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) hL[v][kk] = hR[v][kk] = T(0);
+        }
+        for (int i = 0; i < nm; ++i) {
+          const T pL = mv.fphiT[((size_t)fL * nm + i) * nqf + q];
+          const T pR = mv.fphiT[((size_t)fR * nm + i) * nqf + q];
+          T dL[D], dR[D];
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) {
+            dL[kk] = mv.fdphiT[(((size_t)fL * D + kk) * nm + i) * nqf + q];
+            dR[kk] = mv.fdphiT[(((size_t)fR * D + kk) * nm + i) * nqf + q];
+          }
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            const T a = vL[v * nm + i], b = vR[v * nm + i];
+            tL[v] += a * pL;
+            tR[v] += b * pR;
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) {
+              hL[v][kk] += a * dL[kk];
+              hR[v][kk] += b * dR[kk];
+            }
+          }
+        }
+        const T* cL = Pf + ((size_t)(f0 + fl) * nqf + q) * 2 * PU;
+        const T* cR = cL + PU;
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          uL[v] = S(cL[v], tL[v]);
+          uR[v] = S(cR[v], tR[v]);
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) {
+            gL[v][kk] = S(cL[M + v * D + kk], hL[v][kk]);
+            gR[v][kk] = S(cR[M + v * D + kk], hR[v][kk]);
+          }
+        }
+      }
+    }
+    for (int i = 0; interp && i < nm; ++i) {
       T pL = mv.fphiT[((size_t)fL * nm + i) * nqf + q];
       T pR = mv.fphiT[((size_t)fR * nm + i) * nqf + q];
       T dL[D], dR[D];
@@ -274,10 +322,10 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
                                                                    const float* __restrict__ slots,
                                                                    const float* __restrict__ Src, float sigma,
                                                                    float* __restrict__ out, int* status,
-                                                                   int nqp) {
+                                                                   int nqp, const float* __restrict__ Pv) {
   using T = float;
   using S = typename std::conditional<JVP, Dual<T>, T>::type;
-  constexpr int M = D + 2, NT = 1 + D;
+  constexpr int M = D + 2, NT = 1 + D, PU = M * (1 + D);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = mv.nb, nm = mv.nm, nq = mv.nq, E = mv.E;
   T* Tab = reinterpret_cast<T*>(smem_raw);            // [1 + D][nm][nqp]
@@ -299,7 +347,7 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
   const int bar = 1 + slot;
   for (int e = blockIdx.x * NSLOT + slot; e < E; e += gridDim.x * NSLOT) {
     for (int t = tid; t < nb; t += 256) {
-      sW[t] = W[(size_t)e * nb + t];
+      if (!Pv) sW[t] = W[(size_t)e * nb + t];
       if (JVP) sV[t] = V[(size_t)e * nb + t];
     }
     asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
@@ -312,7 +360,40 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
         for (int kk = 0; kk < D; ++kk) g[v][kk] = T(0);
       }
       const T* tq = Tab + q;
-      for (int i = 0; i < nm; ++i) {
+      bool interp = true;
+      if constexpr (JVP) {
+        if (Pv) {   // primal traces from the cache, interpolate only v
+          interp = false;
+          T tv[M], th[M][D];
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            tv[v] = T(0);
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) th[v][kk] = T(0);
+          }
+          for (int i = 0; i < nm; ++i) {
+            const T p = tq[(size_t)i * nqp];
+            T dp[D];
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) dp[kk] = tq[((size_t)(1 + kk) * nm + i) * nqp];
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+              const T a = sV[v * nm + i];
+              tv[v] += a * p;
+#pragma unroll
+              for (int kk = 0; kk < D; ++kk) th[v][kk] += a * dp[kk];
+            }
+          }
+          const T* c = Pv + ((size_t)e * nq + q) * PU;
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            u[v] = S(c[v], tv[v]);
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) g[v][kk] = S(c[M + v * D + kk], th[v][kk]);
+          }
+        }
+      }
+      for (int i = 0; interp && i < nm; ++i) {
         const T p = tq[(size_t)i * nqp];
         T dp[D];
 #pragma unroll
@@ -392,7 +473,7 @@ static size_t vol_smem(const Mesh& M, int epc, bool jvp) {
 
 template <int D, class T, bool JVP>
 static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T* S, T sigma, T* out,
-                                cudaStream_t st) {
+                                cudaStream_t st, const T* Pv, const T* Pf) {
   MeshView<T> mv = Ms.view<T>();
   Phys<T> ph = Ms.phys_t<T>();
   T* slots = std::is_same<T, double>::value ? (T*)Ms.t64.slots : (T*)Ms.t32.slots;
@@ -403,7 +484,8 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
     allow_max_smem(face_kernel<D, T, JVP>);
   int nfaces = D * Ms.E;
   note_launch();
-  face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc);
+  face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc,
+                                                                    JVP ? Pf : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if constexpr (std::is_same<T, float>::value) {
@@ -417,7 +499,8 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
       const int grid = std::min(nsm, (Ms.E + VOL_SLOTS - 1) / VOL_SLOTS);
       note_launch();
       volume_kernel_st<D, JVP, VOL_SLOTS><<<grid, 256 * VOL_SLOTS, tsm, st>>>(mv, ph, W, V, slots, S, sigma, out,
-                                                                             Ms.status, nqp);
+                                                                             Ms.status, nqp,
+                                                                             JVP ? (const float*)Pv : nullptr);
       return cudaGetLastError();
     }
   }
@@ -433,19 +516,101 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
 }
 
 template <class T>
-cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
-                            T* out, cudaStream_t st) {
+cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
+                            cudaStream_t st, const T* Pv, const T* Pf) {
   if (M.d == 2)
-    return jvp ? run_residual<2, T, true>(M, W, V, S, sigma, out, st)
-               : run_residual<2, T, false>(M, W, V, S, sigma, out, st);
-  return jvp ? run_residual<3, T, true>(M, W, V, S, sigma, out, st)
-             : run_residual<3, T, false>(M, W, V, S, sigma, out, st);
+    return jvp ? run_residual<2, T, true>(M, W, V, S, sigma, out, st, Pv, Pf)
+               : run_residual<2, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr);
+  return jvp ? run_residual<3, T, true>(M, W, V, S, sigma, out, st, Pv, Pf)
+             : run_residual<3, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr);
 }
 
-template cudaError_t launch_residual<double>(const Mesh&, const double*, const double*, const double*,
-                                             double, bool, double*, cudaStream_t);
-template cudaError_t launch_residual<float>(const Mesh&, const float*, const float*, const float*, float,
-                                            bool, float*, cudaStream_t);
+template cudaError_t launch_residual<double>(const Mesh&, const double*, const double*, const double*, double,
+                                             bool, double*, cudaStream_t, const double*, const double*);
+template cudaError_t launch_residual<float>(const Mesh&, const float*, const float*, const float*, float, bool,
+                                            float*, cudaStream_t, const float*, const float*);
+
+// Primal traces of the FP32 state at every volume point, Pv[e][q] = (u, grad u),
+// and at every face point on both sides, Pf[f][q][side] (face f = k E + e joins
+// e, on its xi_k = +1 side, to its +e_k neighbour), in the mode order of the
+// kernels' own interpolation.  Computed once per preconditioner refresh: the
+// smoother's JVPs then interpolate only their direction.
+template <int D>
+__global__ void primal_cache_kernel(MeshView<float> mv, const float* __restrict__ W, float* __restrict__ Pv,
+                                    float* __restrict__ Pf) {
+  constexpr int M = D + 2, PU = M * (1 + D);
+  const int nb = mv.nb, nm = mv.nm, nq = mv.nq, nqf = mv.nqf, E = mv.E;
+  const long nvol = (long)E * nq, nface = (long)D * E * nqf * 2;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nvol + nface; t += (long)gridDim.x * blockDim.x) {
+    float u[M], g[M][D];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      u[v] = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) g[v][kk] = 0.f;
+    }
+    float* dst;
+    if (t < nvol) {
+      const long e = t / nq;
+      const int q = (int)(t - e * nq);
+      const float* w = W + (size_t)e * nb;
+      for (int i = 0; i < nm; ++i) {
+        const float p = mv.vphiT[(size_t)i * nq + q];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const float a = w[v * nm + i];
+          u[v] += a * p;
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) g[v][kk] += a * mv.vdphiT[((size_t)kk * nm + i) * nq + q];
+        }
+      }
+      dst = Pv + (size_t)t * PU;
+    } else {
+      const long r = t - nvol;
+      const int side = (int)(r & 1);
+      const long fq = r >> 1, f = fq / nqf;
+      const int q = (int)(fq - f * nqf), k = (int)(f / E);
+      const long e = f - (long)k * E;
+      const long el = side == 0 ? e : mv.nbr[(e * D + k) * 2 + 1];
+      const int lf = side == 0 ? 2 * k + 1 : 2 * k;
+      const float* w = W + (size_t)el * nb;
+      for (int i = 0; i < nm; ++i) {
+        const float p = mv.fphiT[((size_t)lf * nm + i) * nqf + q];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          const float a = w[v * nm + i];
+          u[v] += a * p;
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) g[v][kk] += a * mv.fdphiT[(((size_t)lf * D + kk) * nm + i) * nqf + q];
+        }
+      }
+      dst = Pf + (size_t)r * PU;
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+      dst[v] = u[v];
+#pragma unroll
+      for (int kk = 0; kk < D; ++kk) dst[M + v * D + kk] = g[v][kk];
+    }
+  }
+}
+
+size_t primal_cache_sizes(const Mesh& M, size_t* nface) {
+  const size_t pu = (size_t)M.m * (1 + M.d);
+  *nface = (size_t)M.d * M.E * M.nqf * 2 * pu;
+  return (size_t)M.E * M.nq * pu;
+}
+
+cudaError_t launch_primal_cache(const Mesh& M, const float* W, float* Pv, float* Pf, cudaStream_t st) {
+  const long tot = (long)M.E * M.nq + (long)M.d * M.E * M.nqf * 2;
+  const int grid = (int)std::min<long>((tot + 255) / 256, 65535L * 4);
+  note_launch();
+  if (M.d == 2)
+    primal_cache_kernel<2><<<grid, 256, 0, st>>>(M.view<float>(), W, Pv, Pf);
+  else
+    primal_cache_kernel<3><<<grid, 256, 0, st>>>(M.view<float>(), W, Pv, Pf);
+  return cudaGetLastError();
+}
 
 // FP64 residual with caller-provided face slots (E * d * 2 * nb doubles) in
 // place of the mesh handle's own: the same two kernels, launched the same way.
@@ -462,7 +627,7 @@ static cudaError_t run_residual_slots(const Mesh& Ms, const double* W, const dou
   int nfaces = D * Ms.E;
   note_launch();
   face_kernel<D, double, false><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, nullptr, slots,
-                                                                            Ms.status, fpc);
+                                                                            Ms.status, fpc, nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int epc = std::max(1, 256 / Ms.nq);

@@ -101,6 +101,13 @@ size_t estimate_bytes(const Key& k) {
     int nu = l == nl - 1 ? k.opts.nu_coarse : std::max(k.opts.nu_pre[l], k.opts.nu_post[l]);
     bytes += (size_t)E * nb * es * (2 * nu + 8);
   }
+  if (k.opts.precision == DG_PREC_MIXED && k.opts.cycle != DG_CYCLE_BJ) {   // primal-trace caches
+    const int nq1 = d.nq1d > 0 ? d.nq1d : d.p + 2;
+    long nq = 1, nqf = 1;
+    for (int i = 0; i < d.dim; ++i) nq *= nq1;
+    for (int i = 1; i < d.dim; ++i) nqf *= nq1;
+    bytes += (size_t)E * (nq + 2 * d.dim * nqf) * m * (1 + d.dim) * 4;
+  }
   return bytes + (64u << 20);                               // tables, probing scratch, slack
 }
 
