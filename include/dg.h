@@ -201,6 +201,32 @@ dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, const double
                          double sigma, const dg_krylov_opts* opts, double* dW,
                          dg_krylov_stats* stats, void* stream);
 
+/* Newton right-hand side of ESDIRK stage i (Sec. 4, eq. NEWTON):
+ *   b = -[ sigma M (Wk - Wn) + racc + R(Wk) ],  sigma = 1/(a_ii dt),  M = |J| I,
+ * racc = sum_{j<i} (a_ij / a_ii) R(W^j) (device, may be NULL when i has no
+ * earlier implicit terms).  Wk (current Newton iterate of the stage), Wn, b:
+ * device FP64; b must not alias the inputs.  sigma > 0. */
+dg_status dg_esdirk3_rhs(dg_mesh mesh, const double* Wk, const double* Wn, double sigma,
+                         const double* racc, double* b, void* stream);
+
+/* One ESDIRK3 time step of M dW/dt + R(W) = 0 (Sec. 4): the four-stage,
+ * third-order, explicit-first-stage, stiffly accurate scheme the paper uses
+ * (Kennedy & Carpenter's ESDIRK3(2)4L[2]SA coefficients).  The preconditioner
+ * `pmg` is refreshed once at Wn with sigma = 1/(a_ii dt) and reused for every
+ * stage and Newton iteration (lagging, Sec. 7.4); each of the three implicit
+ * stages starts from the previous stage and takes `newton` (1..16) Newton
+ * iterations, each an FGMRES solve (dg_fgmres_step with kopts) of eq. NEWTON.
+ * W^{n+1} = the last stage goes to Wout (device FP64, must not alias Wn).
+ * work: caller-owned device scratch of at least 6 * n_dofs doubles
+ * (work_bytes), the stage residuals and the Newton vectors.  Blocks until the
+ * step ends.  stats (host, may be NULL): iterations summed over the 3*newton
+ * solves, ms_total summed, res0/res_final/rho of the last solve.  Returns
+ * DG_OK, DG_ERR_NOT_CONVERGED if some solve stopped above tolerance (the step
+ * still completes), or an error of the calls above. */
+dg_status dg_esdirk3_step(dg_mesh mesh, dg_pmg pmg, const double* Wn, double dt, int newton,
+                          const dg_krylov_opts* kopts, double* work, size_t work_bytes, double* Wout,
+                          dg_krylov_stats* stats, void* stream);
+
 /* Newton right-hand side of one BDF2 step (the form of eq. NEWTON with the
  * BDF2 shift 3/(2 dt) in place of 1/(a_ii dt)):
  *   b = -[ M (3 Wk - 4 Wn + Wnm1) / (2 dt) + R(Wk) ],  M = |J| I.

@@ -22,7 +22,8 @@ BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR, BLOCKS_DIAG = 0, 1, 2
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
-            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh", "dg_residual_noalloc"]
+            "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh", "dg_residual_noalloc",
+            "dg_esdirk3_rhs", "dg_esdirk3_step"]
 
 
 class DGError(RuntimeError):
@@ -91,6 +92,9 @@ def load(path=None):
         "dg_launch_count": [ctypes.POINTER(ctypes.c_ulonglong)],
         "dg_pmg_refresh": [P, P, ctypes.c_double, P],
         "dg_residual_noalloc": [P, P, P, P, P],
+        "dg_esdirk3_rhs": [P, P, P, ctypes.c_double, P, P, P],
+        "dg_esdirk3_step": [P, P, P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(KrylovOpts), P, ctypes.c_size_t,
+                            P, ctypes.POINTER(KrylovStats), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -191,6 +195,11 @@ class Mesh:
         _check("dg_bdf2_rhs", load().dg_bdf2_rhs(self.h, _ptr(Wk), _ptr(Wn), _ptr(Wnm1), float(dt), _ptr(b),
                                                  _stream(stream)))
 
+    def esdirk3_rhs(self, Wk, Wn, sigma, racc, b, stream=None):
+        """b = -[sigma M (Wk - Wn) + racc + R(Wk)] (ESDIRK stage Newton right-hand side)."""
+        _check("dg_esdirk3_rhs", load().dg_esdirk3_rhs(self.h, _ptr(Wk), _ptr(Wn), float(sigma), _ptr(racc),
+                                                       _ptr(b), _stream(stream)))
+
     def axpy(self, alpha, x, y, stream=None):
         _check("dg_axpy", load().dg_axpy(self.h, float(alpha), _ptr(x), _ptr(y), _stream(stream)))
 
@@ -269,6 +278,23 @@ class PMG:
                    ms_total=st.ms_total)
         if raise_on_error and code != DG_OK:
             raise DGError("dg_fgmres_step", code)
+        return out
+
+    def esdirk3_step(self, Wn, dt, Wout, newton=2, restart=30, max_restarts=4, rtol=1e-5, atol=0.0,
+                     work=None, stream=None, raise_on_error=True):
+        """One ESDIRK3 step from Wn into Wout (preconditioner refreshed at Wn and
+        lagged over the step); `work` (device FP64, >= 6 n_dofs) is allocated here
+        when not given.  Returns the summed KrylovStats as a dict."""
+        if work is None:
+            work = Wn.new_empty((6 * Wn.numel(),))
+        ko = KrylovOpts(int(restart), int(max_restarts), float(rtol), float(atol), JVP_EXACT)
+        st = KrylovStats()
+        code = load().dg_esdirk3_step(self.mesh.h, self.h, _ptr(Wn), float(dt), int(newton), ctypes.byref(ko),
+                                      _ptr(work), work.numel() * work.element_size(), _ptr(Wout), ctypes.byref(st),
+                                      _stream(stream))
+        out = dict(iters=st.iters, res_final=st.res_final, status=code, ms_total=st.ms_total)
+        if raise_on_error and code != DG_OK:
+            raise DGError("dg_esdirk3_step", code)
         return out
 
 

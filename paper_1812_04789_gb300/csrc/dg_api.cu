@@ -634,6 +634,87 @@ extern "C" dg_status dg_bdf2_rhs(dg_mesh mesh, const double* Wk, const double* W
   return DG_OK;
 }
 
+namespace dgk {
+// b = -(c (Wk - Wn) + racc + b), b holding R(Wk) on entry; racc may be null
+__global__ void esdirk_rhs_kernel(long N, const double* __restrict__ Wk, const double* __restrict__ Wn,
+                                  const double* __restrict__ racc, double c, double* __restrict__ b) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
+    b[n] = -(c * (Wk[n] - Wn[n]) + (racc ? racc[n] : 0.0) + b[n]);
+}
+
+// ESDIRK3 (four stages, third order, explicit first stage, stiffly accurate):
+// Kennedy & Carpenter's ESDIRK3(2)4L[2]SA coefficients, as published.
+constexpr double ES_G = 1767732205903.0 / 4055673282236.0;
+constexpr double ES_A[4][4] = {
+    {0.0, 0.0, 0.0, 0.0},
+    {ES_G, ES_G, 0.0, 0.0},
+    {2746238789719.0 / 10658868560708.0, -640167445237.0 / 6845629431997.0, ES_G, 0.0},
+    {1471266399579.0 / 7840856788654.0, -4482444167858.0 / 7529755066697.0, 11266239266428.0 / 11593286722821.0,
+     ES_G}};
+}  // namespace dgk
+
+extern "C" dg_status dg_esdirk3_rhs(dg_mesh mesh, const double* Wk, const double* Wn, double sigma,
+                                    const double* racc, double* b, void* stream) {
+  if (!mesh || !Wk || !Wn || !b || b == Wk || b == Wn || b == racc || !(sigma > 0.0)) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Mesh& M = mesh->m;
+  const long N = (long)M.E * M.nb;
+  CK(launch_residual<double>(M, Wk, nullptr, nullptr, 0.0, false, b, st));
+  int gr = (int)std::min<long>((N + 255) / 256, 4096);
+  note_launch();
+  esdirk_rhs_kernel<<<gr, 256, 0, st>>>(N, Wk, Wn, racc, sigma * M.detJ, b);
+  CK(cudaGetLastError());
+  return DG_OK;
+}
+
+extern "C" dg_status dg_esdirk3_step(dg_mesh mesh, dg_pmg pmg, const double* Wn, double dt, int newton,
+                                     const dg_krylov_opts* kopts, double* work, size_t work_bytes, double* Wout,
+                                     dg_krylov_stats* stats, void* stream) {
+  if (!mesh || !pmg || !Wn || !kopts || !work || !Wout || Wout == Wn || !(dt > 0.0) || newton < 1 || newton > 16)
+    return DG_ERR_INVALID;
+  if (pmg->mesh != mesh) return DG_ERR_INVALID;
+  const Mesh& M = mesh->m;
+  const long N = (long)M.E * M.nb;
+  if (work_bytes < sizeof(double) * 6 * (size_t)N) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* R[3] = {work, work + N, work + 2 * N};
+  double* racc = work + 3 * N;
+  double* b = work + 4 * N;
+  double* dW = work + 5 * N;
+  const double sigma = 1.0 / (ES_G * dt);
+  dg_status s = dg_pmg_refresh(pmg, Wn, sigma, stream);   // lagged over the whole step
+  if (s != DG_OK) return s;
+  CK(launch_residual<double>(M, Wn, nullptr, nullptr, 0.0, false, R[0], st));
+  CK(cudaMemcpyAsync(Wout, Wn, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  int iters = 0, solves = 0;
+  dg_status worst = DG_OK;
+  dg_krylov_stats last{};
+  float ms = 0.f;
+  for (int i = 1; i < 4; ++i) {
+    for (int j = 0; j < i; ++j) CK(launch_axpby<double>(N, ES_A[i][j] / ES_A[i][i], R[j], j == 0 ? 0.0 : 1.0, racc, st));
+    for (int it = 0; it < newton; ++it) {
+      if ((s = dg_esdirk3_rhs(mesh, Wout, Wn, sigma, racc, b, stream)) != DG_OK) return s;
+      s = dg_fgmres_step(mesh, pmg, Wout, b, sigma, kopts, dW, &last, stream);
+      if (s != DG_OK && s != DG_ERR_NOT_CONVERGED) return s;
+      if (s != DG_OK) worst = s;
+      iters += last.iters;
+      ms += last.ms_total;
+      ++solves;
+      CK(launch_axpby<double>(N, 1.0, dW, 1.0, Wout, st));
+    }
+    if (i < 3) CK(launch_residual<double>(M, Wout, nullptr, nullptr, 0.0, false, R[i], st));
+  }
+  CK(cudaStreamSynchronize(st));
+  if (stats) {
+    *stats = last;
+    stats->iters = iters;
+    stats->ms_total = ms;
+    stats->status = worst;
+  }
+  (void)solves;
+  return worst;
+}
+
 extern "C" dg_status dg_axpy(dg_mesh mesh, double alpha, const double* x, double* y, void* stream) {
   if (!mesh || !x || !y || x == y) return DG_ERR_INVALID;
   const long N = (long)mesh->m.E * mesh->m.nb;
