@@ -30,7 +30,7 @@ __device__ __forceinline__ int dof(int nm, int v, int i) {
 
 // ---------------------------------------------------------------- face kernel
 template <int D, class T, bool JVP>
-__global__ void __launch_bounds__(128) face_kernel(MeshView<T> mv, Phys<T> ph,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshView<T> mv, Phys<T> ph,
                                                    const T* __restrict__ W,
                                                    const T* __restrict__ V,
                                                    T* __restrict__ slots, int* status, int fpc,
