@@ -1,7 +1,7 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
 
-Bars (written here, derived in the design doc): residual and exact JVP 1e-12 in the
-relative max-norm; block-Jacobi inverses 1e-10 (Dinv_gpu D_oracle = I);
+Bars: residual and exact JVP 1e-12 in the relative max-norm (FP64 evaluation
+of the same quadrature sums in another order; the workload's bar); block-Jacobi inverses 1e-10 (Dinv_gpu D_oracle = I);
 neighbour blocks 1e-12; pMG apply (FP64) 1e-10; FGMRES step (FP64) same
 iteration count +-1 and the updated state within 1e-10 relative L2; mixed
 precision within 1e-6 relative L2 of the FP64 oracle's updated state with at
