@@ -49,23 +49,30 @@ def legendre_orthonormal(nmax, x):
     return P * scale.reshape(shape), dP * scale.reshape(shape)
 
 
-def modes(p, d):
-    """Multi-indices of the total-degree-p space in d dimensions, ordered by
-    total degree, then lexicographically with the first index descending."""
+def modes(p, d, basis="P"):
+    """Multi-indices of the total-degree-p space P_p (basis "P") or of the
+    tensor-product space Q_p (basis "Q", the paper's quadrilateral basis,
+    Sec. 3) in d dimensions, ordered by degree (total degree for P, largest
+    one-dimensional degree for Q), then lexicographically with the first index
+    descending.  Either way the leading modes span the lower-order space of the
+    same kind, which p-multigrid inheritance relies on (Sec. 6.1)."""
     out = []
     for s in range(p + 1):
-        level = [a for a in itertools.product(range(s + 1), repeat=d) if sum(a) == s]
+        if basis == "Q":
+            level = [a for a in itertools.product(range(s + 1), repeat=d) if max(a) == s]
+        else:
+            level = [a for a in itertools.product(range(s + 1), repeat=d) if sum(a) == s]
         level.sort(reverse=True)
         out.extend(level)
     return out
 
 
-def n_modes(p, d):
-    """dim P_p in d dimensions = C(p+d, d) (the paper's prod_i (k+i)/i)."""
-    return math.comb(p + d, d)
+def n_modes(p, d, basis="P"):
+    """dim P_p = C(p+d, d) (the paper's prod_i (k+i)/i) or dim Q_p = (p+1)^d."""
+    return (p + 1) ** d if basis == "Q" else math.comb(p + d, d)
 
 
-def volume_tables(p, d, nq1d):
+def volume_tables(p, d, nq1d, basis="P"):
     """Basis and reference gradients at the tensor GL volume points.
 
     Returns (phi[q, i], dphi[k, q, i], wq[q], xi[q, k]); point index q runs with
@@ -73,7 +80,7 @@ def volume_tables(p, d, nq1d):
     """
     x, w = gauss_legendre(nq1d)
     L, dL = legendre_orthonormal(p, x)
-    md = modes(p, d)
+    md = modes(p, d, basis)
     pts = list(itertools.product(range(nq1d), repeat=d))
     pts = [tuple(reversed(t)) for t in pts]          # first coordinate fastest
     nq = len(pts)
@@ -93,7 +100,7 @@ def volume_tables(p, d, nq1d):
     return phi, dphi, wq, xi
 
 
-def face_tables(p, d, nq1d, k, side):
+def face_tables(p, d, nq1d, k, side, basis="P"):
     """Basis traces and reference gradients on the local face xi_k = side (+-1).
 
     Face points are the tensor GL points of the other d-1 coordinates (in
@@ -104,7 +111,7 @@ def face_tables(p, d, nq1d, k, side):
     x, w = gauss_legendre(nq1d)
     L, dL = legendre_orthonormal(p, x)
     Le, dLe = legendre_orthonormal(p, np.array([float(side)]))
-    md = modes(p, d)
+    md = modes(p, d, basis)
     tang = [kk for kk in range(d) if kk != k]
     pts = list(itertools.product(range(nq1d), repeat=d - 1))
     pts = [tuple(reversed(t)) for t in pts]

@@ -71,7 +71,7 @@ def offdiag_blocks(mesh, ph, W, p_coarse, elems=None, h=1e-30):
     T = np.arange(mesh.E) if elems is None else np.asarray(elems, dtype=np.int64)
     col = colours(mesh)
     d, m, nm = mesh.d, mesh.m, mesh.nm
-    nmc = n_modes(p_coarse, d)
+    nmc = n_modes(p_coarse, d, mesh.space)
     nbc = m * nmc
     O = np.zeros((len(T), d, 2, nbc, nbc))
     for c in range(3):

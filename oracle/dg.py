@@ -36,7 +36,7 @@ from .physics import flux_c, flux_v, visc_K, roe_flux
 class Mesh:
     """Periodic structured mesh with the modal basis tables (Sec. 3)."""
 
-    def __init__(self, dim, n, lo, hi, p, nq1d=None):
+    def __init__(self, dim, n, lo, hi, p, nq1d=None, space="P"):
         self.d = d = int(dim)
         self.n = tuple(int(x) for x in n[:d])
         self.lo = tuple(float(x) for x in lo[:d])
@@ -44,7 +44,8 @@ class Mesh:
         self.p = int(p)
         self.nq1d = int(nq1d) if nq1d else self.p + 2
         self.m = d + 2
-        self.nm = basis.n_modes(self.p, d)
+        self.space = basis_kind = str(space)      # "P": total degree p, "Q": tensor degree p
+        self.nm = basis.n_modes(self.p, d, basis_kind)
         self.nb = self.m * self.nm
         self.E = int(np.prod(self.n))
         self.h = [(self.hi[k] - self.lo[k]) / self.n[k] for k in range(d)]
@@ -52,11 +53,11 @@ class Mesh:
         self.faceJ = [float(np.prod([self.h[kk] / 2.0 for kk in range(d) if kk != k]))
                       for k in range(d)]
         self.metric = [2.0 / hk for hk in self.h]
-        self.phi, self.dphi, self.wq, self.xi = basis.volume_tables(self.p, d, self.nq1d)
+        self.phi, self.dphi, self.wq, self.xi = basis.volume_tables(self.p, d, self.nq1d, basis_kind)
         self.face = {}
         for k in range(d):
             for s in (-1, 1):
-                self.face[(k, s)] = basis.face_tables(self.p, d, self.nq1d, k, s)
+                self.face[(k, s)] = basis.face_tables(self.p, d, self.nq1d, k, s, basis_kind)
         # element multi-indices and periodic face neighbours nbr[e, k, side]
         idx = np.stack(np.unravel_index(np.arange(self.E), tuple(reversed(self.n))), axis=1)
         self.ijk = idx[:, ::-1].copy()                    # (E, d), first index fastest
@@ -218,7 +219,7 @@ def l2_project(mesh, f, nq_extra=3):
     the oracle's own convergence tests (the orthonormal basis makes the
     projection coefficient extraction: W_i = |J|^-1 int_K f phi_i)."""
     nq1d = mesh.p + 1 + nq_extra
-    phi, _, wq, xi = basis.volume_tables(mesh.p, mesh.d, nq1d)
+    phi, _, wq, xi = basis.volume_tables(mesh.p, mesh.d, nq1d, mesh.space)
     c = mesh.centers()
     X = c[:, None, :] + xi[None, :, :] * (np.array(mesh.h) / 2.0)[None, None, :]
     vals = f(X)

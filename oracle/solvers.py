@@ -194,7 +194,7 @@ def pmg_setup(mesh, ph, W, sigma, p_levels, nu_pre=10, nu_post=10, nu_coarse=30)
     from .blocks import diag_blocks, offdiag_blocks, truncate_block, BlockJacobi, bsr_apply
     from .dg import jvp
     d, m = mesh.d, mesh.m
-    nm = [n_modes(p, d) for p in p_levels]
+    nm = [n_modes(p, d, mesh.space) for p in p_levels]
     D0 = diag_blocks(mesh, ph, W, sigma)
     A = [lambda x: jvp(mesh, ph, W, x, sigma)]
     P = [BlockJacobi(D0, m, nm[0])]

@@ -27,17 +27,22 @@ import numpy as np
 SEED = 1812_04789
 
 
-def mode_list(p, d):
+def mode_list(p, d, space="P"):
+    """Mode multi-indices: total degree <= p ("P") or every 1-D degree <= p ("Q"),
+    ordered by degree (total, resp. largest 1-D), then first index descending."""
     out = []
     for s in range(p + 1):
-        lv = [a for a in itertools.product(range(s + 1), repeat=d) if sum(a) == s]
+        if space == "Q":
+            lv = [a for a in itertools.product(range(s + 1), repeat=d) if max(a) == s]
+        else:
+            lv = [a for a in itertools.product(range(s + 1), repeat=d) if sum(a) == s]
         lv.sort(reverse=True)
         out.extend(lv)
     return out
 
 
-def n_modes(p, d):
-    return math.comb(p + d, d)
+def n_modes(p, d, space="P"):
+    return (p + 1) ** d if space == "Q" else math.comb(p + d, d)
 
 
 CONFIGS = {
@@ -57,7 +62,7 @@ CONFIGS = {
 
 
 def make_config(case, dim, n, p, M=0.1, Re=1600.0, dt_conv=0.01, p_levels=None, lo=None,
-                hi=None):
+                hi=None, space="P"):
     """A workload dict of the same shape as CONFIGS entries (smaller meshes for
     tests)."""
     n = tuple(n) + (1,) * (3 - len(n))
@@ -68,7 +73,7 @@ def make_config(case, dim, n, p, M=0.1, Re=1600.0, dt_conv=0.01, p_levels=None, 
         lo = lo or (0.0,) * 3
         hi = hi or (2 * math.pi,) * 3
     return dict(case=case, dim=dim, n=n, lo=lo, hi=hi, p=p, M=M, Re=Re, dt_conv=dt_conv,
-                p_levels=tuple(p_levels) if p_levels else (p,))
+                p_levels=tuple(p_levels) if p_levels else (p,), space=space)
 
 
 def n_elements(cfg):
@@ -77,7 +82,7 @@ def n_elements(cfg):
 
 def state_shape(cfg, p=None):
     d = cfg["dim"]
-    return (n_elements(cfg), d + 2, n_modes(cfg["p"] if p is None else p, d))
+    return (n_elements(cfg), d + 2, n_modes(cfg["p"] if p is None else p, d, cfg.get("space", "P")))
 
 
 def ref_speed_length(cfg, gamma=1.4):
@@ -101,7 +106,8 @@ def time_step(cfg, gamma=1.4):
 
 def mesh_desc(cfg, nq1d=None):
     return dict(dim=cfg["dim"], n=tuple(cfg["n"]), lo=tuple(cfg["lo"]), hi=tuple(cfg["hi"]),
-                p=cfg["p"], nq1d=(cfg["p"] + 2) if nq1d is None else nq1d)
+                p=cfg["p"], nq1d=(cfg["p"] + 2) if nq1d is None else nq1d,
+                space=cfg.get("space", "P"))
 
 
 # ---------------------------------------------------------------- closed forms
@@ -152,7 +158,7 @@ def project(cfg, field, nq_extra=3):
     nq = p + 1 + nq_extra
     x1, w1 = np.polynomial.legendre.leggauss(nq)
     V1 = np.polynomial.legendre.legvander(x1, p) * np.sqrt((2 * np.arange(p + 1) + 1) / 2.0)
-    md = mode_list(p, d)
+    md = mode_list(p, d, cfg.get("space", "P"))
     grids = np.meshgrid(*([np.arange(nq)] * d), indexing="ij")
     aidx = [g.reshape(-1) for g in grids]               # quadrature multi-index
     wq = np.ones(len(aidx[0]))
@@ -194,7 +200,7 @@ def perturbed_state(cfg, seed=SEED, amp=1e-2):
     mode i of degree s has standard deviation amp * |W0| / (1 + s)^2."""
     W = initial_state(cfg)
     rng = np.random.default_rng(seed)
-    deg = np.array([sum(a) for a in mode_list(cfg["p"], cfg["dim"])], dtype=float)
+    deg = np.array([sum(a) for a in mode_list(cfg["p"], cfg["dim"], cfg.get("space", "P"))], dtype=float)
     scale = np.abs(W[:, :, :1]).mean(axis=0, keepdims=True)
     return W + amp * scale * rng.standard_normal(W.shape) / (1.0 + deg) ** 2
 

@@ -8,7 +8,7 @@ from paper_1812_04789_gb300 import workloads as wl
 
 def oracle_mesh(cfg, nq1d=None):
     d = wl.mesh_desc(cfg, nq1d)
-    return Mesh(d["dim"], d["n"], d["lo"], d["hi"], d["p"], d["nq1d"])
+    return Mesh(d["dim"], d["n"], d["lo"], d["hi"], d["p"], d["nq1d"], space=d.get("space", "P"))
 
 
 def oracle_physics(cfg, **kw):

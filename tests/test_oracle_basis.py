@@ -113,3 +113,30 @@ def test_face_trace_matches_volume_function():
                     der = np.array([np.prod([(dL if k3 == kk else L)[al[k3], k3]
                                              for k3 in range(d)]) for al in md])
                     np.testing.assert_allclose(dpf[kk, q], der, atol=1e-13)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_tensor_modes_count_and_hierarchy(d):
+    """Q_p (the paper's quadrilateral basis, Sec. 3): (p+1)^d modes, every 1-D
+    degree <= p, and the leading (p'+1)^d modes span Q_p' (inheritance)."""
+    for p in range(6):
+        md = basis.modes(p, d, "Q")
+        assert len(md) == basis.n_modes(p, d, "Q") == (p + 1) ** d
+        assert len(set(md)) == len(md) and all(max(a) <= p for a in md)
+        for pp in range(p + 1):
+            head = md[: basis.n_modes(pp, d, "Q")]
+            assert sorted(head) == sorted(a for a in md if max(a) <= pp)
+
+
+@pytest.mark.parametrize("d,p", [(2, 3), (3, 2)])
+def test_tensor_volume_orthonormal_and_divergence(d, p):
+    phi, dphi, wq, xi = basis.volume_tables(p, d, p + 2, "Q")
+    np.testing.assert_allclose(phi.T @ (wq[:, None] * phi), np.eye(phi.shape[1]), atol=1e-13)
+    # int_K d(phi_i phi_j)/dxi_k = boundary terms on the faces xi_k = +-1
+    for k in range(d):
+        vol = (dphi[k].T * wq) @ phi + ((phi.T * wq) @ dphi[k])
+        bnd = np.zeros_like(vol)
+        for side in (-1, 1):
+            pf, _, wf = basis.face_tables(p, d, p + 2, k, side, "Q")
+            bnd += side * (pf.T * wf) @ pf
+        np.testing.assert_allclose(vol, bnd, atol=1e-12)

@@ -235,3 +235,71 @@ def test_element_subset_matches_full():
     R = residual(mesh, ph, W)
     sub = np.array([4, 0, 7])
     np.testing.assert_allclose(residual(mesh, ph, W, elems=sub), R[sub], atol=0)
+
+
+Q_CASES = [
+    wl.make_config("tgv", 3, (3, 2, 2), 2, M=0.3, Re=50.0, space="Q"),
+    wl.make_config("vortex", 2, (4, 3), 3, M=0.5, Re=100.0, space="Q"),
+]
+
+
+@pytest.mark.parametrize("cfg", Q_CASES)
+def test_tensor_basis_free_stream_and_conservation(cfg):
+    mesh, ph = oracle_mesh(cfg), oracle_physics(cfg)
+    assert mesh.nm == (cfg["p"] + 1) ** cfg["dim"]
+    W = uniform_state(cfg)
+    assert np.abs(residual(mesh, ph, W)).max() <= 1e-13 * np.abs(W).max()
+    W = wl.perturbed_state(cfg, amp=0.05)
+    R = residual(mesh, ph, W)
+    assert np.abs(R[:, :, 0].sum(axis=0)).max() <= 1e-13 * np.abs(R).max() * mesh.E
+
+
+def test_tensor_basis_contains_total_degree_solution():
+    """P_p is a subspace of Q_p: for the inviscid residual (mu = 0: no BR2
+    lifting, whose projection space differs between the two bases, eq. re) a
+    state with only total-degree-<= p modes has the same residual on those
+    modes in either basis."""
+    cfg_p = wl.make_config("vortex", 2, (3, 3), 2, M=0.5, Re=100.0)
+    cfg_q = dict(cfg_p, space="Q")
+    mp, mq = oracle_mesh(cfg_p), oracle_mesh(cfg_q)
+    ph = Physics(gamma=1.4, mu=0.0, roe_delta=0.1)
+    Wp = wl.perturbed_state(cfg_p, amp=0.05)
+    mdp, mdq = basis.modes(2, 2), basis.modes(2, 2, "Q")
+    idx = [mdq.index(a) for a in mdp]
+    Wq = np.zeros((mp.E, mp.m, mq.nm))
+    Wq[:, :, idx] = Wp
+    Rp, Rq = residual(mp, ph, Wp), residual(mq, ph, Wq)
+    assert relmax(Rq[:, :, idx], Rp) <= 1e-12
+
+
+def test_tensor_basis_steady_vortex_rate_and_jvp():
+    g = 1.4
+    beta, Rv = 0.2, 0.5
+
+    def field(X):
+        dx, dy = X[..., 0] - 5.0, X[..., 1] - 5.0
+        r2 = (dx * dx + dy * dy) / Rv**2
+        U = 0.5 * math.sqrt(g)
+        u = -U * beta * dy / Rv * np.exp(-r2 / 2)
+        v = U * beta * dx / Rv * np.exp(-r2 / 2)
+        T = 1.0 - U * U * beta * beta / (2 * g / (g - 1)) * np.exp(-r2)
+        rho = T ** (1 / (g - 1))
+        return [rho, rho * u, rho * v, rho * T / (g - 1) + 0.5 * rho * (u * u + v * v)]
+    errs = []
+    p = 2
+    for n in (8, 16, 32):
+        cfg = wl.make_config("vortex", 2, (n, n), p, space="Q")
+        mesh = oracle_mesh(cfg)
+        ph = Physics(gamma=g, mu=0.0, roe_delta=0.1)
+        W = l2_project(mesh, field)
+        R = residual(mesh, ph, W) / mesh.detJ
+        errs.append(math.sqrt(mesh.detJ * np.sum(R * R)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] >= p - 0.3, (errs, rates)
+    cfg = Q_CASES[1]
+    mesh, ph = oracle_mesh(cfg), oracle_physics(cfg)
+    W = wl.perturbed_state(cfg, amp=0.05)
+    v = wl.random_vector(W.shape)
+    h = 1e-6
+    fd = (residual(mesh, ph, W + h * v) - residual(mesh, ph, W - h * v)) / (2 * h)
+    assert relmax(jvp(mesh, ph, W, v, 0.0), fd) <= 1e-7
