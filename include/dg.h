@@ -52,13 +52,22 @@ typedef enum {
 /* Periodic structured mesh of boxes on [lo, hi] (quads for dim 2, hexes for
  * dim 3) with n[k] elements per direction, polynomial degree p (0..8) and nq1d
  * Gauss-Legendre points per direction on volumes and faces (0 => p + 2).
+ * space: DG_SPACE_P, orthonormal Legendre products of total degree <= p
+ * (C(p+d, d) modes), or DG_SPACE_Q, the tensor-product space of degree <= p in
+ * each direction ((p+1)^d modes; the paper's quadrilateral basis, Sec. 3).
+ * Modes are ordered by degree (total for P, largest one-dimensional for Q),
+ * then lexicographically with the first index descending, so the leading
+ * modes of a level span every lower level of the same space (Sec. 6.1).
  * Sec. 3 (broken space, eq. BSpace) and Sec. 3.1 (DG discretisation). */
+#define DG_SPACE_P 0
+#define DG_SPACE_Q 1
 typedef struct {
   int dim;
   int n[3];
   double lo[3], hi[3];
   int p;
   int nq1d;
+  int space;
 } dg_mesh_desc;
 
 /* Gas and discretisation constants (Sec. 2 closure; Sec. 3.1): ratio of specific

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID", 2: "DG_ERR_OOM", 3: "DG_ERR_CUD
 JVP_EXACT, JVP_FD, JVP_FD_SCALED, JVP_EXACT_FP32 = 0, 1, 2, 3
 CYCLE_FMG, CYCLE_V, CYCLE_BJ = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
+SPACE_P, SPACE_Q = 0, 1
 BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR, BLOCKS_DIAG = 0, 1, 2
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
@@ -34,7 +35,8 @@ class DGError(RuntimeError):
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
-                ("hi", ctypes.c_double * 3), ("p", ctypes.c_int), ("nq1d", ctypes.c_int)]
+                ("hi", ctypes.c_double * 3), ("p", ctypes.c_int), ("nq1d", ctypes.c_int),
+                ("space", ctypes.c_int)]
 
 
 class PhysicsDesc(ctypes.Structure):
@@ -138,7 +140,7 @@ class Mesh:
     """Owns a dg_mesh handle (periodic structured mesh + basis tables)."""
 
     def __init__(self, dim, n, lo, hi, p, nq1d=0, gamma=1.4, Pr=0.72, mu=0.0, Rgas=1.0, eta=0.0,
-                 roe_delta=0.1, stream=None):
+                 roe_delta=0.1, stream=None, space="P"):
         lib = load()
         d = MeshDesc()
         d.dim = dim
@@ -148,6 +150,7 @@ class Mesh:
         for k in range(3):
             d.n[k], d.lo[k], d.hi[k] = int(n[k]), float(lo[k]), float(hi[k])
         d.p, d.nq1d = int(p), int(nq1d)
+        d.space = SPACE_Q if space == "Q" else SPACE_P
         ph = PhysicsDesc(gamma, Pr, mu, Rgas, eta, roe_delta)
         h = P()
         _check("dg_mesh_create", lib.dg_mesh_create(ctypes.byref(d), ctypes.byref(ph), _stream(stream),
@@ -164,7 +167,8 @@ class Mesh:
         """From workloads.mesh_desc(...) / workloads.physics(...) dicts."""
         return cls(desc["dim"], desc["n"], desc["lo"], desc["hi"], desc["p"], desc.get("nq1d", 0),
                    gamma=phys["gamma"], Pr=phys["Pr"], mu=phys["mu"], Rgas=phys["Rgas"],
-                   eta=phys.get("eta", 0.0) or 0.0, roe_delta=phys["roe_delta"], stream=stream)
+                   eta=phys.get("eta", 0.0) or 0.0, roe_delta=phys["roe_delta"], stream=stream,
+                   space=desc.get("space", "P"))
 
     @property
     def shape(self):
@@ -335,6 +339,7 @@ def mesh_desc_struct(desc):
     for k in range(3):
         d.n[k], d.lo[k], d.hi[k] = int(n[k]), float(lo[k]), float(hi[k])
     d.p, d.nq1d = int(desc["p"]), int(desc.get("nq1d", 0))
+    d.space = SPACE_Q if desc.get("space", "P") == "Q" else SPACE_P
     return d
 
 

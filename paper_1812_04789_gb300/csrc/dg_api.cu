@@ -182,7 +182,10 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
     Level<T>& L = mg.lv[l];
     L.p = o.p_level[l];
     long c = 1;  // n_m = C(p + d, d)
-    for (int i = 1; i <= M.d; ++i) c = c * (L.p + i) / i;
+    if (M.desc.space == DG_SPACE_Q)
+      for (int i = 1; i <= M.d; ++i) c *= L.p + 1;
+    else
+      for (int i = 1; i <= M.d; ++i) c = c * (L.p + i) / i;
     L.nm = (int)c;
     L.nb = M.m * L.nm;
     L.N = (long)M.E * L.nb;

@@ -74,8 +74,16 @@ static void legendre(int pmax, double z, double* L, double* dL) {
 
 // Total-degree multi-indices ordered by degree, then lexicographically with
 // the first index descending.
-static std::vector<std::array<int, 3>> mode_list(int p, int d) {
+static std::vector<std::array<int, 3>> mode_list(int p, int d, int space) {
   std::vector<std::array<int, 3>> out;
+  if (space == DG_SPACE_Q) {   // largest 1-D degree s, then descending lexicographic
+    for (int s = 0; s <= p; ++s)
+      for (int a = s; a >= 0; --a)
+        for (int b = s; b >= 0; --b)
+          for (int c = (d == 3 ? s : 0); c >= 0; --c)
+            if (std::max(a, std::max(b, c)) == s) out.push_back({a, b, d == 3 ? c : 0});
+    return out;
+  }
   for (int s = 0; s <= p; ++s) {
     std::vector<std::array<int, 3>> lv;
     for (int a = s; a >= 0; --a) {
@@ -175,7 +183,7 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
   M.p = desc->p;
   M.nq1d = desc->nq1d > 0 ? desc->nq1d : desc->p + 2;
   const int d = M.d, p = M.p, nq1 = M.nq1d;
-  auto modes = mode_list(p, d);
+  auto modes = mode_list(p, d, desc->space);
   M.nm = (int)modes.size();
   M.nb = M.m * M.nm;
   M.nq = 1;
@@ -366,6 +374,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_physics* 
   if (!desc || !phys) return DG_ERR_INVALID;
   if (desc->dim != 2 && desc->dim != 3) return DG_ERR_INVALID;
   if (desc->p < 0 || desc->p > 8) return DG_ERR_INVALID;
+  if (desc->space != DG_SPACE_P && desc->space != DG_SPACE_Q) return DG_ERR_INVALID;
   int nq1 = desc->nq1d > 0 ? desc->nq1d : desc->p + 2;
   if (nq1 < desc->p + 1 || nq1 > 12) return DG_ERR_INVALID;
   long E = 1;

@@ -35,8 +35,12 @@ struct Key {
   dg_physics phys;
   dg_pmg_opts opts;
   bool operator==(const Key& o) const {
-    return memcmp(&desc, &o.desc, sizeof(desc)) == 0 && memcmp(&phys, &o.phys, sizeof(phys)) == 0 &&
-           memcmp(&opts, &o.opts, sizeof(opts)) == 0;
+    // field by field: the descriptor has tail padding a caller need not clear
+    const dg_mesh_desc& a = desc;
+    const dg_mesh_desc& b = o.desc;
+    bool same = a.dim == b.dim && a.p == b.p && a.nq1d == b.nq1d && a.space == b.space;
+    for (int k = 0; k < 3; ++k) same = same && a.n[k] == b.n[k] && a.lo[k] == b.lo[k] && a.hi[k] == b.hi[k];
+    return same && memcmp(&phys, &o.phys, sizeof(phys)) == 0 && memcmp(&opts, &o.opts, sizeof(opts)) == 0;
   }
 };
 
@@ -81,7 +85,7 @@ size_t estimate_bytes(const Key& k) {
   for (int i = 0; i < d.dim; ++i) E *= d.n[i];
   auto nmodes = [&](int p) {
     long c = 1;
-    for (int i = 1; i <= d.dim; ++i) c = c * (p + i) / i;
+    for (int i = 1; i <= d.dim; ++i) c = d.space == DG_SPACE_Q ? c * (p + 1) : c * (p + i) / i;
     return c;
   };
   const int m = d.dim + 2;
