@@ -45,6 +45,7 @@ struct Tables {
   T* fd_w = nullptr;         // finite-difference JVP scratch: W + h v
   T* fd_r = nullptr;         // finite-difference JVP scratch: R(W + h v)
   T* fd_o = nullptr;         // FP32 JVP mode scratch: the product before conversion
+  T* l1d = nullptr;          // Q space: L[p+1][nq1d], dL[p+1][nq1d] (reference), w[nq1d]
 };
 
 // Plan of the tensor-core block probe (FP32 blocks): seed variables are taken
@@ -70,6 +71,7 @@ struct Mesh {
   TcPlan tc;                 // tensor-core probe plan and its element-independent tables:
   float* tc_test = nullptr;  //   test rows [point][kind][nmp] (weights, signs, lifting folded in)
   float* tc_trial = nullptr; //   trial operand per K step [nks][hi, lo][npad x 8] in MMA layout
+  int* qidx = nullptr;       // Q space: mode index of the tensor index (a, b[, c]), a fastest-varying last
   int* status = nullptr;     // device status word
   double* scal = nullptr;    // device scalars for the FD JVP (norms, h)
   double* partials = nullptr;// reduction partials for the FD JVP norms
@@ -86,6 +88,13 @@ struct Mesh {
 template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
                             T* out, cudaStream_t st, const T* Pv = nullptr, const T* Pf = nullptr);
+
+// Volume part (+ face slots, + sigma |J| V or - S) by sum factorisation for the
+// tensor-product space; cudaErrorNotSupported when the mesh is not Q_p or the
+// element's stages do not fit shared memory (the direct kernel then runs).
+template <class T>
+cudaError_t launch_volume_q(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
+                            cudaStream_t st);
 
 // Primal traces (u, grad u) of an FP32 state at the volume points and on both
 // sides of every face point; primal_cache_sizes returns the volume cache's

@@ -350,6 +350,30 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
     return err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
   if ((err = upload_tables<float>(M, M.t32, tabs)) != cudaSuccess)
     return err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+  if (desc->space == DG_SPACE_Q) {   // one-dimensional factors for sum factorisation
+    const int n1 = p + 1;
+    std::vector<double> l1d((size_t)2 * n1 * nq1 + nq1);
+    for (int a = 0; a < n1; ++a)
+      for (int q = 0; q < nq1; ++q) {
+        l1d[(size_t)a * nq1 + q] = L1(q, a);
+        l1d[(size_t)(n1 + a) * nq1 + q] = dL1(q, a);
+      }
+    for (int q = 0; q < nq1; ++q) l1d[(size_t)2 * n1 * nq1 + q] = wg[q];
+    if ((err = upload<double>(M, l1d, &M.t64.l1d)) != cudaSuccess) return DG_ERR_OOM;
+    if ((err = upload<float>(M, l1d, &M.t32.l1d)) != cudaSuccess) return DG_ERR_OOM;
+    int nt = 1;
+    for (int k = 0; k < d; ++k) nt *= n1;
+    std::vector<int> qi(nt, -1);
+    for (size_t i = 0; i < modes.size(); ++i) {
+      const auto& md = modes[i];   // md[k]: degree in direction k
+      int t = 0;
+      for (int k = d - 1; k >= 0; --k) t = t * n1 + md[k];   // t = a0 + n1 (a1 + n1 a2)
+      qi[t] = (int)i;
+    }
+    if (cudaMalloc((void**)&M.qidx, sizeof(int) * nt) != cudaSuccess) return DG_ERR_OOM;
+    M.allocs.push_back(M.qidx);
+    if (cudaMemcpy(M.qidx, qi.data(), sizeof(int) * nt, cudaMemcpyHostToDevice) != cudaSuccess) return DG_ERR_CUDA;
+  }
   if (cudaMalloc((void**)&M.status, sizeof(int)) != cudaSuccess) return DG_ERR_OOM;
   M.allocs.push_back(M.status);
   if (cudaMemset(M.status, 0, sizeof(int)) != cudaSuccess) return DG_ERR_CUDA;

@@ -488,6 +488,11 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
                                                                     JVP ? Pf : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (Ms.desc.space == DG_SPACE_Q) {   // sum factorisation when it fits
+    cudaError_t eq = launch_volume_q<T>(Ms, W, V, S, sigma, JVP, out, st);
+    if (eq != cudaErrorNotSupported) return eq;
+    (void)cudaGetLastError();
+  }
   if constexpr (std::is_same<T, float>::value) {
     size_t tsm;
     int nqp;
