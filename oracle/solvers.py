@@ -184,12 +184,14 @@ def bdf2_rhs(mesh, RW, Wk, Wn, Wnm1, dt):
     return mesh.detJ * (3.0 * Wk - 4.0 * Wn + Wnm1) / (2.0 * dt) + RW
 
 
-def pmg_setup(mesh, ph, W, sigma, p_levels, nu_pre=10, nu_post=10, nu_coarse=30):
+def pmg_setup(mesh, ph, W, sigma, p_levels, nu_pre=10, nu_post=10, nu_coarse=30, coarse="bj", order="mdf"):
     """Assemble the p-multigrid preconditioner once (lagged, Sec. 7.4):
     fine diagonal blocks, neighbour blocks at the first coarse order (Sec. 6.3:
     off-diagonal blocks are only needed at coarse order), inheritance by
     truncation for every coarser level, PLU of every diagonal block.
-    Level 0 applies the matrix-free exact K; levels >= 1 the inherited blocks."""
+    Level 0 applies the matrix-free exact K; levels >= 1 the inherited blocks.
+    coarse="bilu": the coarsest level's smoother is preconditioned by block
+    ILU(0) in the given order (Table MGSettings) instead of block Jacobi."""
     from .basis import n_modes
     from .blocks import diag_blocks, offdiag_blocks, truncate_block, BlockJacobi, bsr_apply
     from .dg import jvp
@@ -205,4 +207,9 @@ def pmg_setup(mesh, ph, W, sigma, p_levels, nu_pre=10, nu_post=10, nu_coarse=30)
             Ol = truncate_block(O1, m, nm[1], nm[l])
             A.append(lambda x, Dl=Dl, Ol=Ol: bsr_apply(mesh, Dl, Ol, x))
             P.append(BlockJacobi(Dl, m, nm[l]))
+        if coarse == "bilu":
+            from .bilu import BILU
+            P[-1] = BILU(mesh, Dl, Ol, m, nm[-1], order)
+    elif coarse != "bj":
+        raise ValueError("block ILU needs a coarse level with neighbour blocks")
     return PMG(A, P, nm, nu_pre, nu_post, nu_coarse)
