@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-esdirk", action="store_true")
+    ap.add_argument("--no-bilu", action="store_true")
     return ap.parse_args()
 
 
@@ -108,7 +109,7 @@ class Clocks:
 class Stepper:
     """One BDF2 implicit step on the device through the library's C ABI."""
 
-    def __init__(self, B, torch, cfg, precision, stream, W0, Wm1):
+    def __init__(self, B, torch, cfg, precision, stream, W0, Wm1, coarse=0, order=0):
         self.B, self.torch = B, torch
         self.cfg = cfg
         self.stream = stream
@@ -118,7 +119,8 @@ class Stepper:
         self.sigma = 1.5 / self.dt
         o = bench_opts(cfg)
         self.opts = B.pmg_opts(o["p_levels"], nu_pre=o["nu_pre"], nu_post=o["nu_post"],
-                               nu_coarse=o["nu_coarse"], cycle=o["cycle"], precision=precision)
+                               nu_coarse=o["nu_coarse"], cycle=o["cycle"], precision=precision,
+                               coarse=coarse, order=order)
         dev = torch.device("cuda", torch.cuda.current_device())
         self.W0 = torch.from_numpy(W0).to(dev)
         self.Wm1 = torch.from_numpy(Wm1).to(dev)
@@ -194,6 +196,31 @@ def esdirk3_steps(torch, B, stepper, steps, newton, stream, flush):
             "fgmres_iters_per_solve": statistics.mean(its), "steps": steps,
             "scheme": "ESDIRK3 (4 stages, 3 implicit), %d Newton per stage, mixed-precision pMG lagged "
                       "over the step" % newton}
+
+
+def coarse_bilu_steps(torch, B, cfg, stream, W0, Wm1, newton, flush):
+    """The coarsest smoother preconditioned by element block ILU(0) (Table
+    MGSettings) instead of block Jacobi, mixed precision, on the headline case:
+    one BDF2 step per element order after one warm-up step (device time,
+    FGMRES iterations per solve, substitution levels), and one pMG application."""
+    out = {}
+    r = torch.from_numpy(wl.random_vector(W0.shape, 41)).cuda()
+    z = torch.empty_like(r)
+    for name, coarse, order in (("bj", B.COARSE_BJ, 0), ("natural", B.COARSE_BILU, B.ORDER_NATURAL),
+                                ("colour", B.COARSE_BILU, B.ORDER_COLOUR), ("mdf", B.COARSE_BILU, B.ORDER_MDF)):
+        st = Stepper(B, torch, cfg, B.PREC_MIXED, stream, W0, Wm1, coarse=coarse, order=order)
+        times = timed_steps(torch, st, 1, 1, newton, stream, flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st.pmg.apply(r, z, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = {"ms_per_step": times[0], "fgmres_iters_per_solve": statistics.mean(st.iters),
+                     "pmg_apply_ms": e0.elapsed_time(e1),
+                     "levels": st.pmg.bilu_order(stream=stream)[1] if coarse == B.COARSE_BILU else None}
+        st.pmg.close()
+        st.mesh.close()
+    return out
 
 
 def kernel_roofline(torch, B, stepper, stream, peaks):
@@ -452,6 +479,7 @@ def run_gb300(args):
         roof = kernel_roofline(torch, B, head, stream, peaks)
         esd = None if args.no_esdirk else esdirk3_steps(torch, B, head, max(1, min(args.steps, 3)), args.newton,
                                                         stream, flush)
+        bilu = None if args.no_bilu else coarse_bilu_steps(torch, B, cfg, stream, W0, Wm1, args.newton, flush)
         # end to end through the public API with pinned host buffers
         e2e = None
         if not args.no_e2e:
@@ -505,6 +533,7 @@ def run_gb300(args):
         "jvp_fp64": roof["jvp_fp64"],
         "probe_tc": roof.get("probe_tc"),
         "esdirk3": esd,
+        "coarse_bilu": bilu,
         "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
     if not args.no_batched:

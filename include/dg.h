@@ -141,10 +141,20 @@ dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma,
 #define DG_PREC_FP64 0
 #define DG_PREC_MIXED 1     /* FP32 smoothers, blocks and fine JVP inside the preconditioner */
 
+#define DG_COARSE_BJ 0      /* coarsest smoother: GMRES(element block Jacobi) */
+#define DG_COARSE_BILU 1    /* coarsest smoother: GMRES(element block ILU(0)) (Table MGSettings) */
+#define DG_ORDER_MDF 0      /* block ILU(0) in minimum discarded fill order (Sec. 6.3) */
+#define DG_ORDER_NATURAL 1  /* element index order */
+#define DG_ORDER_COLOUR 2   /* greedy multicolour order (few substitution levels) */
+
 /* p-multigrid options (Sec. 6; Table MGSettings).  p_level[0] must equal the
  * mesh degree and the levels must decrease strictly.  Every smoother is GMRES
- * right-preconditioned by element block Jacobi; nu_pre/nu_post (0..64) per level
- * (ignored on the coarsest), nu_coarse (1..64) on the coarsest level. */
+ * right-preconditioned by element block Jacobi, except the coarsest one with
+ * coarse_precond = DG_COARSE_BILU (needs n_levels >= 2, the cycle FMG or V, no
+ * periodic direction of exactly 3 elements, and a coarsest block of at most
+ * 64 rows in FP64 / 90 in FP32); nu_pre/nu_post (0..64) per level (ignored on
+ * the coarsest), nu_coarse (1..64) on the coarsest level.  A zero-initialised
+ * tail (coarse_precond, coarse_order) selects block Jacobi. */
 typedef struct {
   int n_levels;
   int p_level[8];
@@ -152,6 +162,8 @@ typedef struct {
   int cycle;
   int precision;
   int fgmres_restart;   /* size of the outer FGMRES workspace allocated here (0 => 30, <= 64) */
+  int coarse_precond;   /* DG_COARSE_BJ or DG_COARSE_BILU */
+  int coarse_order;     /* DG_ORDER_*: element order of the block ILU(0) */
 } dg_pmg_opts;
 
 /* Assemble the preconditioner at state W and shift sigma (once per time step:
@@ -304,6 +316,30 @@ dg_status dg_server_destroy(dg_server server);
 /* Synchronise `stream`, return the mesh's device status word (DG_OK if no
  * device-side problem was recorded since the last call) and clear it. */
 dg_status dg_status_sync(dg_mesh mesh, void* stream);
+
+/* Element order and substitution levels of a block ILU(0) (Sec. 6.3), on the
+ * host.  Graph: n_elem elements with n_faces face neighbours each, nbr[e *
+ * n_faces + s] (a neighbour equal to e is a self coupling and ignored; one
+ * neighbour reached through several faces counts once).  kind DG_ORDER_MDF
+ * takes c[e * n_faces + s] = ||A_ee^{-1} A_e,nbr||_F for the first face of each
+ * distinct neighbour (other entries unread; c may be NULL for the other kinds):
+ * the next element is the one whose elimination drops the least fill, weight
+ * w_i = sqrt(sum (c_ji c_ik)^2) over ordered pairs (j, k) of distinct unordered
+ * neighbours of i that are not neighbours of each other, ties to the lowest
+ * index, the neighbours' weights updated after each step.  DG_ORDER_NATURAL:
+ * index order; DG_ORDER_COLOUR: greedy colouring in index order, then sorted by
+ * (colour, index).  Outputs (host, caller-owned, n_elem entries): order[p] = the
+ * element at position p, level[e] = 1 + the largest level of e's neighbours
+ * ordered before it (0 if none); *n_levels = number of levels.  No GPU use.
+ * DG_ERR_INVALID on a bad argument or neighbour index. */
+dg_status dg_bilu_order(int n_elem, int n_faces, const int* nbr, const double* c, int kind, int* order,
+                        int* level, int* n_levels);
+
+/* The element order and level count the handle's coarsest block ILU(0) uses
+ * now (after the last setup or refresh; host copies, order: n_elem entries or
+ * NULL).  Synchronises `stream` first.  DG_ERR_INVALID if the handle has no
+ * block ILU(0). */
+dg_status dg_pmg_bilu_order(dg_pmg pmg, int* order, int* n_levels, void* stream);
 
 /* Sizes of the pMG workspace in bytes (blocks, vectors), for memory budgeting. */
 dg_status dg_pmg_bytes(dg_pmg pmg, size_t* block_bytes, size_t* vector_bytes);

@@ -20,11 +20,13 @@ CYCLE_FMG, CYCLE_V, CYCLE_BJ = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 SPACE_P, SPACE_Q = 0, 1
 BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR, BLOCKS_DIAG = 0, 1, 2
+COARSE_BJ, COARSE_BILU = 0, 1
+ORDER_MDF, ORDER_NATURAL, ORDER_COLOUR = 0, 1, 2
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
             "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh", "dg_residual_noalloc",
-            "dg_esdirk3_rhs", "dg_esdirk3_step"]
+            "dg_esdirk3_rhs", "dg_esdirk3_step", "dg_bilu_order", "dg_pmg_bilu_order"]
 
 
 class DGError(RuntimeError):
@@ -47,7 +49,8 @@ class PhysicsDesc(ctypes.Structure):
 class PmgOpts(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_int), ("p_level", ctypes.c_int * 8), ("nu_pre", ctypes.c_int * 8),
                 ("nu_post", ctypes.c_int * 8), ("nu_coarse", ctypes.c_int), ("cycle", ctypes.c_int),
-                ("precision", ctypes.c_int), ("fgmres_restart", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("coarse_precond", ctypes.c_int),
+                ("coarse_order", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -97,6 +100,10 @@ def load(path=None):
         "dg_esdirk3_rhs": [P, P, P, ctypes.c_double, P, P, P],
         "dg_esdirk3_step": [P, P, P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(KrylovOpts), P, ctypes.c_size_t,
                             P, ctypes.POINTER(KrylovStats), P],
+        "dg_bilu_order": [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                          ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_int)],
+        "dg_pmg_bilu_order": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -219,7 +226,7 @@ def launch_count():
 
 
 def pmg_opts(p_levels, nu_pre=10, nu_post=10, nu_coarse=30, cycle=CYCLE_FMG, precision=PREC_FP64,
-             fgmres_restart=30):
+             fgmres_restart=30, coarse=COARSE_BJ, order=ORDER_MDF):
     o = PmgOpts()
     o.n_levels = len(p_levels)
     for l, p in enumerate(p_levels):
@@ -230,7 +237,30 @@ def pmg_opts(p_levels, nu_pre=10, nu_post=10, nu_coarse=30, cycle=CYCLE_FMG, pre
     o.cycle = int(cycle)
     o.precision = int(precision)
     o.fgmres_restart = int(fgmres_restart)
+    o.coarse_precond = int(coarse)
+    o.coarse_order = int(order)
     return o
+
+
+def bilu_order(nbr, kind, c=None):
+    """Host ordering of a block ILU(0) (dg_bilu_order): nbr int array
+    [n_elem, n_faces], c float array of the same shape (MDF only).  Returns
+    (order, level, n_levels) as numpy arrays / int."""
+    import numpy as np
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    E, nf = nbr.shape
+    order = np.zeros(E, dtype=np.int32)
+    level = np.zeros(E, dtype=np.int32)
+    nl = ctypes.c_int()
+    cp = None
+    if c is not None:
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        cp = c.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ip = ctypes.POINTER(ctypes.c_int)
+    _check("dg_bilu_order", load().dg_bilu_order(E, nf, nbr.ctypes.data_as(ip), cp, int(kind),
+                                                 order.ctypes.data_as(ip), level.ctypes.data_as(ip),
+                                                 ctypes.byref(nl)))
+    return order, level, nl.value
 
 
 class PMG:
@@ -259,6 +289,15 @@ class PMG:
 
     def apply(self, r, z, stream=None):
         _check("dg_pmg_apply", load().dg_pmg_apply(self.h, _ptr(r), _ptr(z), _stream(stream)))
+
+    def bilu_order(self, stream=None):
+        """(order, n_levels) of the coarsest block ILU(0) now in use."""
+        import numpy as np
+        order = np.zeros(self.mesh.E, dtype=np.int32)
+        nl = ctypes.c_int()
+        _check("dg_pmg_bilu_order", load().dg_pmg_bilu_order(self.h, order.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                             ctypes.byref(nl), _stream(stream)))
+        return order, nl.value
 
     def bytes(self):
         a, b = ctypes.c_size_t(), ctypes.c_size_t()

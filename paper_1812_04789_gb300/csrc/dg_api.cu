@@ -95,8 +95,9 @@ cudaError_t MG<T>::op(int l, const T* x, T* y, cudaStream_t st) {
   return launch_bsr<T>(L.Dop, L.O, L.cs, L.co_t, mesh->nbr, mesh->d, x, y, L.nb, mesh->E, st);
 }
 
-// SMOOTH / SOLVE: nu iterations of GMRES right-preconditioned by block Jacobi,
-// from the current x (Algorithm 2), no restart.
+// SMOOTH / SOLVE: nu iterations of GMRES right-preconditioned by block Jacobi
+// (block ILU(0) on the coarsest level when asked: Table MGSettings), from the
+// current x (Algorithm 2), no restart.
 template <class T>
 cudaError_t MG<T>::smooth(int l, const T* b, T* x, int nu, cudaStream_t st) {
   Level<T>& L = lv[l];
@@ -104,8 +105,12 @@ cudaError_t MG<T>::smooth(int l, const T* b, T* x, int nu, cudaStream_t st) {
   CKE(op(l, x, L.r, st));
   CKE(launch_axpby<T>(L.N, 1.0, b, -1.0, L.r, st));           // r = b - A x
   CKE(K.start(L.r, st));
+  const bool ilu = bilu && l == (int)lv.size() - 1;   // block ILU(0) on the coarsest level
   for (int j = 0; j < nu; ++j) {
-    CKE(launch_block_apply<T>(L.Dinv, L.bs, L.inv_t, K.Vj(j), K.Zj(j), L.nb, mesh->E, st));
+    if (ilu)
+      CKE(launch_bilu_apply<T>(*this, K.Vj(j), K.Zj(j), st));
+    else
+      CKE(launch_block_apply<T>(L.Dinv, L.bs, L.inv_t, K.Vj(j), K.Zj(j), L.nb, mesh->E, st));
     CKE(op(l, K.Zj(j), K.w, st));
     CKE(K.arnoldi(j, st));
   }
@@ -222,6 +227,28 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
     CK(dalloc(mg.allocs, (void**)&mg.Pv, sizeof(T) * nv, &h->vector_bytes));
     CK(dalloc(mg.allocs, (void**)&mg.Pf, sizeof(T) * nf, &h->vector_bytes));
   }
+  if (o.coarse_precond == DG_COARSE_BILU) {
+    const Level<T>& C = mg.lv.back();
+    const int nf = 2 * M.d;
+    mg.bilu = 1;
+    mg.bl_kind = o.coarse_order;
+    if (!bilu_plan(mg)) return DG_ERR_INVALID;
+    CK(dalloc(mg.allocs, (void**)&mg.Sinv, sizeof(T) * (size_t)M.E * C.nb * C.nb, &h->block_bytes));
+    CK(dalloc(mg.allocs, (void**)&mg.bl_pos, sizeof(int) * M.E, &h->vector_bytes));
+    CK(dalloc(mg.allocs, (void**)&mg.bl_ptr, sizeof(int) * (M.E + 1), &h->vector_bytes));
+    CK(dalloc(mg.allocs, (void**)&mg.bl_el, sizeof(int) * M.E, &h->vector_bytes));
+    CK(dalloc(mg.allocs, (void**)&mg.bl_nlev, sizeof(int), &h->vector_bytes));
+    CK(dalloc(mg.allocs, (void**)&mg.bl_c, sizeof(double) * M.E * nf, &h->vector_bytes));
+    mg.h_nbr.resize((size_t)M.E * nf);
+    CK(cudaMemcpy(mg.h_nbr.data(), M.nbr, sizeof(int) * M.E * nf, cudaMemcpyDeviceToHost));
+    mg.h_c.assign((size_t)M.E * nf, 0.0);
+    mg.h_order.assign(M.E, 0);
+    mg.h_level.assign(M.E, 0);
+    mg.h_pos.assign(M.E, 0);
+    mg.h_el.assign(M.E, 0);
+    mg.h_ptr.assign(M.E + 1, 0);
+    mg.h_nlev = 0;
+  }
   // probing caches live in global memory when they exceed shared memory
   bool fits = true;
   size_t tot = probe_scratch_elems<T>(M, nl > 1 ? mg.lv[1].nm : 0, &fits);
@@ -265,6 +292,7 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
   }
   for (int l = 0; l < nl; ++l)
     CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, mg.lv[l].bs, M.E, M.status, &mg.lv[l].inv_t, st));
+  if (mg.bilu) CK(bilu_refresh<T>(mg, st));
   return DG_OK;
 }
 
@@ -315,17 +343,26 @@ extern "C" dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, do
 // Capture one preconditioner application (every level, every smoother
 // iteration: a few thousand small launches) as a CUDA graph on fixed staging
 // buffers.  The graph reads the handle's blocks and state through pointers, so
-// dg_pmg_refresh does not invalidate it.  DG_PMG_NO_GRAPH=1 disables it.
+// a refresh at the same shift keeps it; the shift itself is a by-value kernel
+// argument, so a refresh at another shift captures it again.
+// DG_PMG_NO_GRAPH=1 disables it.
 static dg_status capture_apply_graph(dg_pmg h) {
   const char* env = getenv("DG_PMG_NO_GRAPH");
   if (env && env[0] == '1') return DG_OK;
   const long N0 = (long)h->mesh->m.E * h->mesh->m.nb;
-  if (h->precision == DG_PREC_FP64) {
-    if (dalloc(h->allocs, (void**)&h->r64, sizeof(double) * N0, &h->vector_bytes) != cudaSuccess ||
-        dalloc(h->allocs, (void**)&h->z64, sizeof(double) * N0, &h->vector_bytes) != cudaSuccess)
-      return DG_ERR_OOM;
+  if (!h->cap_stream) {
+    if (h->precision == DG_PREC_FP64) {
+      if (dalloc(h->allocs, (void**)&h->r64, sizeof(double) * N0, &h->vector_bytes) != cudaSuccess ||
+          dalloc(h->allocs, (void**)&h->z64, sizeof(double) * N0, &h->vector_bytes) != cudaSuccess)
+        return DG_ERR_OOM;
+    }
+    CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   }
-  CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+  h->graph_sigma = h->sigma;
   unsigned long long l0 = __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED);
   CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
   cudaError_t e = h->precision == DG_PREC_FP64 ? h->mg64.apply(h->r64, h->z64, h->cap_stream)
@@ -347,6 +384,15 @@ static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
   if (o->cycle != DG_CYCLE_FMG && o->cycle != DG_CYCLE_V && o->cycle != DG_CYCLE_BJ) return DG_ERR_INVALID;
   if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
   if (o->fgmres_restart < 0 || o->fgmres_restart > 64) return DG_ERR_INVALID;
+  if (o->coarse_precond != DG_COARSE_BJ && o->coarse_precond != DG_COARSE_BILU) return DG_ERR_INVALID;
+  if (o->coarse_precond == DG_COARSE_BILU) {
+    // neighbour blocks exist from level 1; the pivot-block form of ILU(0)
+    // needs a face graph without triangles (no periodic direction of 3)
+    if (o->cycle == DG_CYCLE_BJ || o->n_levels < 2) return DG_ERR_INVALID;
+    if (o->coarse_order < DG_ORDER_MDF || o->coarse_order > DG_ORDER_COLOUR) return DG_ERR_INVALID;
+    for (int k = 0; k < mesh->m.d; ++k)
+      if (mesh->m.desc.n[k] == 3) return DG_ERR_INVALID;
+  }
   if (o->cycle == DG_CYCLE_BJ) return o->p_level[0] == mesh->m.p || o->n_levels == 0 ? DG_OK : DG_ERR_INVALID;
   if (o->n_levels < 1 || o->n_levels > 8) return DG_ERR_INVALID;
   if (o->p_level[0] != mesh->m.p) return DG_ERR_INVALID;
@@ -437,6 +483,7 @@ extern "C" dg_status dg_pmg_refresh(dg_pmg h, const double* W, double sigma, voi
   h->sigma = sigma;
   dg_status s = h->precision == DG_PREC_FP64 ? compute_mg<double>(h, h->mg64, W, st)
                                              : compute_mg<float>(h, h->mg32, W, st);
+  if (s == DG_OK && h->graph_exec && h->graph_sigma != sigma) s = capture_apply_graph(h);
   return s;
 }
 
@@ -469,6 +516,18 @@ static dg_status pmg_apply_impl(dg_pmg h, const double* r, double* z, cudaStream
 extern "C" dg_status dg_pmg_apply(dg_pmg h, const double* r, double* z, void* stream) {
   if (!h || !r || !z || r == z) return DG_ERR_INVALID;
   return pmg_apply_impl(h, r, z, (cudaStream_t)stream);
+}
+
+extern "C" dg_status dg_pmg_bilu_order(dg_pmg h, int* order, int* n_levels, void* stream) {
+  if (!h || !n_levels) return DG_ERR_INVALID;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DG_ERR_CUDA;
+  const bool f64 = h->precision == DG_PREC_FP64;
+  const int on = f64 ? h->mg64.bilu : h->mg32.bilu;
+  if (!on) return DG_ERR_INVALID;
+  const std::vector<int>& o = f64 ? h->mg64.h_order : h->mg32.h_order;
+  *n_levels = f64 ? h->mg64.h_nlev : h->mg32.h_nlev;
+  if (order) std::copy(o.begin(), o.end(), order);
+  return DG_OK;
 }
 
 extern "C" dg_status dg_pmg_bytes(dg_pmg h, size_t* block_bytes, size_t* vector_bytes) {

@@ -246,11 +246,37 @@ struct MG {
   T* Pv = nullptr;           // primal traces of W for the fine JVPs (mixed precision;
   T* Pf = nullptr;           //   refreshed with the blocks), else null
   std::vector<void*> allocs;
+  // element block ILU(0) preconditioning the coarsest smoother (DG_COARSE_BILU)
+  int bilu = 0, bl_kind = 0;  // on / DG_ORDER_* of the element order
+  T* Sinv = nullptr;          // [E][nb][nb] row-major: inverses of the ILU(0) pivot blocks
+  int* bl_pos = nullptr;      // device [E]: position of every element in the order
+  int* bl_ptr = nullptr;      // device [E + 1]: level l = bl_el[bl_ptr[l] .. bl_ptr[l + 1])
+  int* bl_el = nullptr;       // device [E]: elements by level, in order within a level
+  int* bl_nlev = nullptr;     // device [1]: number of levels (read by the kernels)
+  double* bl_c = nullptr;     // device [E][2d]: MDF reduced weights
+  int bl_warps = 0, bl_chunk = 0, bl_resident = 0;   // launch plan (bilu_plan)
+  std::vector<int> h_nbr, h_order, h_level, h_ptr, h_el, h_pos;
+  std::vector<double> h_c;
+  int h_nlev = 0, h_nlev_buf = 0;
   cudaError_t op(int l, const T* x, T* y, cudaStream_t st);
   cudaError_t smooth(int l, const T* b, T* x, int nu, cudaStream_t st);
   cudaError_t mg_v(int l, cudaStream_t st);           // on lv[l].b, lv[l].x
   cudaError_t apply(const T* r, T* z, cudaStream_t st);
 };
+
+// Element block ILU(0) of the coarsest level (csrc/dg_bilu.cu).  bilu_order_host:
+// the host ordering of dg_bilu_order, returns the level count or -1.
+// bilu_plan: launch plan for the level's block size (false: too large).
+// bilu_refresh: order (MDF: from the level's blocks, one device-to-host copy
+// and a host synchronisation; natural / colour: once) and factorisation, after
+// the level's blocks and inverses.  launch_bilu_apply: z = (L U)^{-1} r.
+int bilu_order_host(int E, int nf, const int* nbr, const double* c, int kind, int* order, int* level);
+template <class T>
+bool bilu_plan(MG<T>& mg);
+template <class T>
+cudaError_t bilu_refresh(MG<T>& mg, cudaStream_t st);
+template <class T>
+cudaError_t launch_bilu_apply(const MG<T>& mg, const T* r, T* z, cudaStream_t st);
 
 }  // namespace dgk
 
@@ -279,6 +305,7 @@ struct dg_pmg_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   unsigned long long graph_kernels = 0;
+  double graph_sigma = 0;    // the shift the graph was captured with (a by-value kernel argument)
   std::vector<void*> allocs;
   size_t block_bytes = 0, vector_bytes = 0;
 };

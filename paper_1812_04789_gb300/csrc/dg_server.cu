@@ -105,6 +105,10 @@ size_t estimate_bytes(const Key& k) {
     int nu = l == nl - 1 ? k.opts.nu_coarse : std::max(k.opts.nu_pre[l], k.opts.nu_post[l]);
     bytes += (size_t)E * nb * es * (2 * nu + 8);
   }
+  if (k.opts.coarse_precond == DG_COARSE_BILU && nl >= 2) {   // block ILU(0) pivot inverses + order
+    const long nbc = m * nmodes(k.opts.p_level[nl - 1]);
+    bytes += (size_t)E * nbc * nbc * es + (size_t)E * (2 * d.dim * 8 + 16);
+  }
   if (k.opts.precision == DG_PREC_MIXED && k.opts.cycle != DG_CYCLE_BJ) {   // primal-trace caches
     const int nq1 = d.nq1d > 0 ? d.nq1d : d.p + 2;
     long nq = 1, nqf = 1;

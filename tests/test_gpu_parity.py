@@ -199,6 +199,29 @@ def test_pmg_apply_parity(cycle):
     assert relmax(z.cpu().numpy(), ref) <= 1e-10
 
 
+@pytest.mark.parametrize("precision", [B.PREC_FP64, B.PREC_MIXED])
+def test_refresh_at_a_new_shift_matches_a_fresh_setup(precision):
+    """dg_pmg_refresh with another sigma (an ESDIRK stage after a BDF2 setup):
+    the captured application takes the new shift, bitwise as a fresh setup."""
+    cfg = CASES["tgv3d_p2_3x2x4"]
+    W0, W1 = wl.initial_state(cfg), wl.perturbed_state(cfg)
+    s0 = 1.5 / wl.time_step(cfg)
+    opts = B.pmg_opts((2, 1, 0), nu_pre=3, nu_post=3, nu_coarse=5, precision=precision)
+    m = gpu_mesh(cfg)
+    a = B.PMG(m, dev(W0), s0, opts)
+    a.refresh(dev(W1), 2.5 * s0)
+    b = B.PMG(m, dev(W1), 2.5 * s0, opts)
+    r = dev(wl.random_vector(W0.shape, 23))
+    za, zb = torch.empty_like(r), torch.empty_like(r)
+    a.apply(r, za)
+    b.apply(r, zb)
+    assert m.status_sync() == B.DG_OK
+    assert torch.equal(za, zb)
+    if precision == B.PREC_FP64:
+        ref = _oracle_pmg(cfg, W1, 2.5 * s0, (2, 1, 0), 3, 5).mg_full(wl.random_vector(W0.shape, 23))
+        assert relmax(za.cpu().numpy(), ref) <= 1e-10
+
+
 def _bdf2_problem(cfg):
     om, oph = oracle_mesh(cfg), oracle_physics(cfg)
     W = wl.initial_state(cfg)
