@@ -17,6 +17,7 @@ Modules
   dg       -- mesh, residual R(W) of eq. (dg_ns) with BR2 (eqs. visc_flux, re),
               exact JVP by complex step, FD JVP of eq. (DG-mf)
   blocks   -- Jacobian blocks (diagonal and neighbour), inheritance (Sec. 5.1), PLU
+  tri      -- DG on periodic triangulations, full-order Dubiner basis, blocks and pMG (Sec. 3)
   bilu     -- block ILU(0) of the coarsest level, MDF / natural / colour orders (Sec. 6.3)
   solvers  -- GMRES(BJ) smoother, MG_V (Alg. 2), MG_full (Alg. 1), FGMRES,
               BDF2 Newton step

@@ -13,7 +13,12 @@ Workloads
   * isentropic vortex advected by a uniform stream (Sec. 7.1 of the paper,
     rescaled from [0, 0.1]^2 to [0, 10]^2: R = 0.5, beta = 1/50, centre (5, 5));
   * Taylor-Green vortex on [0, 2 pi]^3 (standard literature definition; the
-    paper has 2-D cases only).
+    paper has 2-D cases only);
+  * the vortex on a periodic triangulation (a seeded, jittered quad lattice cut
+    into triangles, the paper's triangular grids of Sec. 7.2 with the full-order
+    basis): vertex lists and lattice shifts only, the connectivity is left to
+    the consumer; modal states in the orthonormal Dubiner basis, projected
+    with scipy's Jacobi polynomials.
 Nondimensionalisation: rho_inf = p_inf = T_inf = R_gas = 1, c_inf = sqrt(gamma);
 vortex: U_inf = M sqrt(gamma), mu = U_inf L / Re with L = 10 (domain size);
 TGV: V0 = M sqrt(gamma), mu = V0 / Re (L = 1).  Time steps are given in
@@ -257,3 +262,105 @@ def serving_requests(count=32, seed=1812, max_dofs=None):
         cfg["dofs"] = dofs
         out.append(cfg)
     return out
+
+
+# ---------------------------------------------------------------- triangles
+def tri_config(n, p, M=0.5, Re=1000.0, dt_conv=0.05, p_levels=None, lo=(0.0, 0.0), hi=(10.0, 10.0),
+               jitter=0.15, seed=SEED):
+    """The isentropic-vortex workload on a periodic triangulation (the paper's
+    quadrilateral grid split into triangles, full-order P_p basis, Sec. 7.2):
+    n = (n0, n1) quads, each cut into two triangles."""
+    return dict(case="vortex", dim=2, mesh="tri", n=(int(n[0]), int(n[1]), 1), lo=(lo[0], lo[1], 0.0),
+                hi=(hi[0], hi[1], 1.0), p=p, M=M, Re=Re, dt_conv=dt_conv,
+                p_levels=tuple(p_levels) if p_levels else (p,), jitter=jitter, seed=seed, space="tri")
+
+
+def tri_mesh(cfg):
+    """Seeded periodic triangulation of [lo, hi]^2: an n0 x n1 vertex lattice
+    displaced by a periodic jitter (uniform in +-jitter of the spacing per
+    coordinate), every lattice quad split into two counter-clockwise triangles
+    along a seeded diagonal.  Returns dict(X (nv, 2) vertex coordinates, vertex
+    id = i + n0 j; tri (E, 3) vertex ids; shift (E, 3, 2) lattice shifts: corner
+    k of triangle e sits at X[tri[e, k]] + shift[e, k] * (hi - lo)).  Triangles
+    2q and 2q + 1 come from quad q = i + n0 j."""
+    n0, n1 = cfg["n"][0], cfg["n"][1]
+    lo = np.array(cfg["lo"][:2], dtype=np.float64)
+    hi = np.array(cfg["hi"][:2], dtype=np.float64)
+    h = (hi - lo) / np.array([n0, n1])
+    rng = np.random.default_rng(cfg.get("seed", SEED))
+    jit = cfg.get("jitter", 0.15) * h[None, None, :] * rng.uniform(-1.0, 1.0, size=(n1, n0, 2))
+    flips = rng.integers(0, 2, size=(n1, n0))
+    ii, jj = np.meshgrid(np.arange(n0), np.arange(n1))
+    X = np.stack([lo[0] + ii * h[0], lo[1] + jj * h[1]], axis=-1) + jit          # (n1, n0, 2)
+    X = X.reshape(-1, 2)
+
+    def corner(i, j):
+        return (i % n0) + n0 * (j % n1), (i // n0, j // n1)
+
+    tri, shift = [], []
+    for j in range(n1):
+        for i in range(n0):
+            A, B, C, D = corner(i, j), corner(i + 1, j), corner(i + 1, j + 1), corner(i, j + 1)
+            pair = ((A, B, C), (A, C, D)) if flips[j, i] == 0 else ((A, B, D), (B, C, D))
+            for t in pair:
+                tri.append([c[0] for c in t])
+                shift.append([c[1] for c in t])
+    return dict(X=X, tri=np.array(tri, dtype=np.int64), shift=np.array(shift, dtype=np.int64), lo=lo, hi=hi)
+
+
+def tri_modes(p):
+    """(i, j) of the Dubiner modes: total degree i + j, then i descending."""
+    return [(i, q - i) for q in range(p + 1) for i in range(q, -1, -1)]
+
+
+def tri_state_shape(cfg):
+    return (2 * cfg["n"][0] * cfg["n"][1], 4, (cfg["p"] + 1) * (cfg["p"] + 2) // 2)
+
+
+def tri_physics(cfg, **kw):
+    """physics() with the BR2 penalty n_faces + 1 = 4 of a triangle."""
+    kw.setdefault("eta", 4.0)
+    return physics(cfg, **kw)
+
+
+def tri_project(cfg, field, nq_extra=3):
+    """Modal coefficients of the L2 projection of field(X) onto the
+    orthonormal Dubiner basis of every triangle (scipy's Jacobi polynomials,
+    collapsed Gauss-Legendre rule with p + 1 + nq_extra points per direction)."""
+    from scipy.special import eval_jacobi
+    p = cfg["p"]
+    msh = tri_mesh(cfg)
+    L = msh["hi"] - msh["lo"]
+    V = msh["X"][msh["tri"]] + msh["shift"] * L[None, None, :]               # (E, 3, 2)
+    nq = p + 1 + nq_extra
+    x, w = np.polynomial.legendre.leggauss(nq)
+    a, b = np.tile(x, nq), np.repeat(x, nq)
+    wq = np.tile(w, nq) * np.repeat(w, nq) * (1.0 - b) / 2.0
+    r, s = (1.0 + a) * (1.0 - b) / 2.0 - 1.0, b
+    psi = np.zeros((len(wq), len(tri_modes(p))))
+    for t, (i, j) in enumerate(tri_modes(p)):
+        na = 2.0 / (2 * i + 1)
+        nb_ = 2.0 ** (2 * i + 2) / (2 * j + 2 * i + 2)
+        psi[:, t] = (math.sqrt(2.0) * eval_jacobi(i, 0, 0, a) / math.sqrt(na)
+                     * eval_jacobi(j, 2 * i + 1, 0, b) / math.sqrt(nb_) * (1.0 - b) ** i)
+    lam1, lam2 = (r + 1.0) / 2.0, (s + 1.0) / 2.0
+    Xq = V[:, None, 0, :] + lam1[None, :, None] * (V[:, None, 1, :] - V[:, None, 0, :]) \
+        + lam2[None, :, None] * (V[:, None, 2, :] - V[:, None, 0, :])
+    vals = field(Xq)
+    W = np.zeros((len(V), 4, psi.shape[1]))
+    for v in range(4):
+        W[:, v, :] = (vals[v] * wq) @ psi
+    return W
+
+
+def tri_initial_state(cfg, t=0.0, gamma=1.4):
+    return tri_project(cfg, lambda X: vortex_field(X, cfg, t=t, gamma=gamma))
+
+
+def tri_perturbed_state(cfg, seed=SEED, amp=1e-2):
+    """tri_initial_state plus seeded noise, standard deviation amp |W0| / (1 + degree)^2."""
+    W = tri_initial_state(cfg)
+    rng = np.random.default_rng(seed)
+    deg = np.array([i + j for i, j in tri_modes(cfg["p"])], dtype=float)
+    scale = np.abs(W[:, :, :1]).mean(axis=0, keepdims=True)
+    return W + amp * scale * rng.standard_normal(W.shape) / (1.0 + deg) ** 2
