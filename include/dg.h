@@ -89,6 +89,35 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_physics* phys, void*
                          dg_mesh* out);
 dg_status dg_mesh_destroy(dg_mesh mesh);
 
+/* A periodic triangulation of the box [lo, hi]^2 with the full-order space
+ * P_p on every triangle (Sec. 3: total degree <= k on triangular grids; the
+ * quadrilateral grids of Sec. 7.2 split into triangles).  Host inputs, read
+ * during the call: X[n_vert][2] vertex coordinates; tri[n_tri][3] vertex ids
+ * of each triangle, counter-clockwise; shift[n_tri][3][2] integer lattice
+ * shifts, corner k of triangle e at X[tri[e][k]] + shift[e][k] * (hi - lo).
+ * Edges are matched by their vertex pair and relative shift: every edge must
+ * belong to exactly two triangles (periodic, no boundary).  Basis:
+ * orthonormal Dubiner polynomials on the reference triangle (-1,-1), (1,-1),
+ * (-1,1), ordered by total degree i + j, then i descending; state layout
+ * W[e][v][i] as for dg_mesh_create; nq1d (0 => p + 2) points per direction of
+ * the collapsed Gauss rule and per edge; the BR2 penalty eta_br2 = 0 means 4
+ * (n_faces + 1).  Such a handle serves dg_residual, dg_jvp (exact modes),
+ * dg_mesh_info and dg_status_sync; the p-multigrid, the BDF2 / ESDIRK3
+ * right-hand sides, the FD JVP and dg_residual_noalloc return DG_ERR_INVALID.
+ * DG_ERR_INVALID on bad sizes, indices, a clockwise or degenerate triangle or
+ * an edge not shared by exactly two triangles. */
+typedef struct {
+  int n_vert;
+  const double* X;
+  int n_tri;
+  const int* tri;
+  const int* shift;
+  double lo[2], hi[2];
+  int p;
+  int nq1d;
+} dg_tri_desc;
+dg_status dg_mesh_create_tri(const dg_tri_desc* desc, const dg_physics* phys, void* stream, dg_mesh* out);
+
 /* Sizes: elements, modes per variable, variables (m), total DOFs E*m*n_m. */
 dg_status dg_mesh_info(dg_mesh mesh, int* n_elem, int* n_modes, int* n_vars, size_t* n_dofs);
 

@@ -26,7 +26,7 @@ ORDER_MDF, ORDER_NATURAL, ORDER_COLOUR = 0, 1, 2
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
             "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh", "dg_residual_noalloc",
-            "dg_esdirk3_rhs", "dg_esdirk3_step", "dg_bilu_order", "dg_pmg_bilu_order"]
+            "dg_esdirk3_rhs", "dg_esdirk3_step", "dg_bilu_order", "dg_pmg_bilu_order", "dg_mesh_create_tri"]
 
 
 class DGError(RuntimeError):
@@ -39,6 +39,13 @@ class MeshDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("lo", ctypes.c_double * 3),
                 ("hi", ctypes.c_double * 3), ("p", ctypes.c_int), ("nq1d", ctypes.c_int),
                 ("space", ctypes.c_int)]
+
+
+class TriDesc(ctypes.Structure):
+    _fields_ = [("n_vert", ctypes.c_int), ("X", ctypes.POINTER(ctypes.c_double)), ("n_tri", ctypes.c_int),
+                ("tri", ctypes.POINTER(ctypes.c_int)), ("shift", ctypes.POINTER(ctypes.c_int)),
+                ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2), ("p", ctypes.c_int),
+                ("nq1d", ctypes.c_int)]
 
 
 class PhysicsDesc(ctypes.Structure):
@@ -104,6 +111,7 @@ def load(path=None):
                           ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_int)],
         "dg_pmg_bilu_order": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P],
+        "dg_mesh_create_tri": [ctypes.POINTER(TriDesc), ctypes.POINTER(PhysicsDesc), P, ctypes.POINTER(P)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -168,6 +176,45 @@ class Mesh:
         _check("dg_mesh_info", lib.dg_mesh_info(h, ctypes.byref(E), ctypes.byref(nm), ctypes.byref(m),
                                                 ctypes.byref(N)))
         self.E, self.nm, self.m, self.ndofs = E.value, nm.value, m.value, N.value
+
+    @classmethod
+    def triangles(cls, X, tri, shift, lo, hi, p, nq1d=0, gamma=1.4, Pr=0.72, mu=0.0, Rgas=1.0, eta=0.0,
+                  roe_delta=0.1, stream=None):
+        """A periodic triangulation (dg_mesh_create_tri): X (nv, 2) vertex
+        coordinates, tri (E, 3) counter-clockwise vertex ids, shift (E, 3, 2)
+        integer lattice shifts, box [lo, hi]^2, full-order degree p."""
+        import numpy as np
+        lib = load()
+        Xc = np.ascontiguousarray(X, dtype=np.float64)
+        Tc = np.ascontiguousarray(tri, dtype=np.int32)
+        Sc = np.ascontiguousarray(shift, dtype=np.int32)
+        d = TriDesc()
+        d.n_vert, d.n_tri = len(Xc), len(Tc)
+        d.X = Xc.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.tri = Tc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d.shift = Sc.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        for k in range(2):
+            d.lo[k], d.hi[k] = float(lo[k]), float(hi[k])
+        d.p, d.nq1d = int(p), int(nq1d)
+        ph = PhysicsDesc(gamma, Pr, mu, Rgas, eta, roe_delta)
+        h = P()
+        _check("dg_mesh_create_tri", lib.dg_mesh_create_tri(ctypes.byref(d), ctypes.byref(ph), _stream(stream),
+                                                            ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.h = h
+        self.dim, self.p = 2, p
+        E, nm, m, N = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check("dg_mesh_info", lib.dg_mesh_info(h, ctypes.byref(E), ctypes.byref(nm), ctypes.byref(m),
+                                                ctypes.byref(N)))
+        self.E, self.nm, self.m, self.ndofs = E.value, nm.value, m.value, N.value
+        return self
+
+    @classmethod
+    def from_tri_workload(cls, mesh, phys, p, stream=None):
+        """From workloads.tri_mesh(...) / workloads.tri_physics(...) dicts."""
+        return cls.triangles(mesh["X"], mesh["tri"], mesh["shift"], mesh["lo"], mesh["hi"], p,
+                             gamma=phys["gamma"], Pr=phys["Pr"], mu=phys["mu"], Rgas=phys["Rgas"],
+                             eta=phys.get("eta", 0.0) or 0.0, roe_delta=phys["roe_delta"], stream=stream)
 
     @classmethod
     def from_workload(cls, desc, phys, stream=None):

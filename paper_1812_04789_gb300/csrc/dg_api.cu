@@ -335,7 +335,7 @@ extern "C" dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, do
     return DG_OK;
   }
   if (mode != DG_JVP_FD && mode != DG_JVP_FD_SCALED) return DG_ERR_INVALID;
-  if (!R_W || R_W == Kv) return DG_ERR_INVALID;
+  if (!R_W || R_W == Kv || mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;
   CK(fd_jvp(mesh->m, W, R_W, sigma, v, Kv, mode == DG_JVP_FD ? 0 : 1, st));
   return DG_OK;
 }
@@ -381,6 +381,7 @@ static dg_status capture_apply_graph(dg_pmg h) {
 }
 
 static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
+  if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;   // blocks of structured meshes only
   if (o->cycle != DG_CYCLE_FMG && o->cycle != DG_CYCLE_V && o->cycle != DG_CYCLE_BJ) return DG_ERR_INVALID;
   if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
   if (o->fgmres_restart < 0 || o->fgmres_restart > 64) return DG_ERR_INVALID;
@@ -685,6 +686,7 @@ __global__ void bdf2_rhs_kernel(long N, const double* __restrict__ Wk, const dou
 extern "C" dg_status dg_bdf2_rhs(dg_mesh mesh, const double* Wk, const double* Wn, const double* Wnm1, double dt,
                                  double* b, void* stream) {
   if (!mesh || !Wk || !Wn || !Wnm1 || !b || b == Wk || b == Wn || b == Wnm1 || !(dt > 0.0)) return DG_ERR_INVALID;
+  if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;   // one |J| per mesh
   cudaStream_t st = (cudaStream_t)stream;
   const Mesh& M = mesh->m;
   const long N = (long)M.E * M.nb;
@@ -718,6 +720,7 @@ constexpr double ES_A[4][4] = {
 extern "C" dg_status dg_esdirk3_rhs(dg_mesh mesh, const double* Wk, const double* Wn, double sigma,
                                     const double* racc, double* b, void* stream) {
   if (!mesh || !Wk || !Wn || !b || b == Wk || b == Wn || b == racc || !(sigma > 0.0)) return DG_ERR_INVALID;
+  if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;   // one |J| per mesh
   cudaStream_t st = (cudaStream_t)stream;
   const Mesh& M = mesh->m;
   const long N = (long)M.E * M.nb;

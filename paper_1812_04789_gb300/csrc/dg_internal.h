@@ -48,6 +48,17 @@ struct Tables {
   T* l1d = nullptr;          // Q space: L[p+1][nq1d], dL[p+1][nq1d] (reference), w[nq1d]
 };
 
+// Triangle-mesh tables of one precision (csrc/dg_tri.cu): per-triangle
+// geometry and the reference basis on the collapsed rule and the edges.
+template <class T>
+struct TriTab {
+  T *geo = nullptr, *egeo = nullptr;            // [E][5] inverse Jacobian + |J|; [E][3][3] normal, |J_F|
+  T *vphi = nullptr, *vdphi = nullptr, *vw = nullptr;
+  T *ephi = nullptr, *edphi = nullptr, *ew = nullptr, *P = nullptr;
+};
+
+enum : int { DG_MESH_STRUCTURED = 0, DG_MESH_TRI = 1 };
+
 // Plan of the tensor-core block probe (FP32 blocks): seed variables are taken
 // in groups of G whose accumulators, rows (w, v, i') x npad columns in
 // 128-row tiles, fit the 512 TMEM columns; points are taken jq at a time,
@@ -72,6 +83,11 @@ struct Mesh {
   float* tc_test = nullptr;  //   test rows [point][kind][nmp] (weights, signs, lifting folded in)
   float* tc_trial = nullptr; //   trial operand per K step [nks][hi, lo][npad x 8] in MMA layout
   int* qidx = nullptr;       // Q space: mode index of the tensor index (a, b[, c]), a fastest-varying last
+  int kind = DG_MESH_STRUCTURED;
+  int* tnbr = nullptr;       // triangles: device [E][3] neighbour across each local edge
+  int* tnbrf = nullptr;      //   and that neighbour's local edge
+  TriTab<double> tr64;
+  TriTab<float> tr32;
   int* status = nullptr;     // device status word
   double* scal = nullptr;    // device scalars for the FD JVP (norms, h)
   double* partials = nullptr;// reduction partials for the FD JVP norms
@@ -88,6 +104,12 @@ struct Mesh {
 template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
                             T* out, cudaStream_t st, const T* Pv = nullptr, const T* Pf = nullptr);
+
+// Residual / exact JVP on a triangle mesh (csrc/dg_tri.cu), same contract.
+template <class T>
+cudaError_t launch_residual_tri(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
+                                cudaStream_t st);
+void free_mesh(Mesh& M);
 
 // Volume part (+ face slots, + sigma |J| V or - S) by sum factorisation for the
 // tensor-product space; cudaErrorNotSupported when the mesh is not Q_p or the

@@ -128,7 +128,7 @@ static cudaError_t upload_tables(Mesh& M, Tables<T>& t, const std::vector<double
   return cudaSuccess;
 }
 
-static void free_mesh(Mesh& M) {
+void free_mesh(Mesh& M) {
   for (void* p : M.allocs) cudaFree(p);
   M.allocs.clear();
 }

@@ -53,6 +53,7 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh mesh, const double* W, const do
                                          void* stream) {
   if (!mesh || !W || !R || R == W || (S && S == R)) return DG_ERR_INVALID;
   const dgk::Mesh& M = mesh->m;
+  if (M.kind != dgk::DG_MESH_STRUCTURED) return DG_ERR_INVALID;
   const size_t need = (size_t)M.E * M.d * 2 * M.nb;
   if (need > NOALLOC_MAX_SLOTS) return DG_ERR_INVALID;
   double* slots = nullptr;

@@ -523,6 +523,7 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
 template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
                             cudaStream_t st, const T* Pv, const T* Pf) {
+  if (M.kind == DG_MESH_TRI) return launch_residual_tri<T>(M, W, V, S, sigma, jvp, out, st);
   if (M.d == 2)
     return jvp ? run_residual<2, T, true>(M, W, V, S, sigma, out, st, Pv, Pf)
                : run_residual<2, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr);
