@@ -92,7 +92,7 @@ template <class T>
 cudaError_t MG<T>::op(int l, const T* x, T* y, cudaStream_t st) {
   if (l == 0) return launch_residual<T>(*mesh, W, x, nullptr, sigma, true, y, st, Pv, Pf);
   Level<T>& L = lv[l];
-  return launch_bsr<T>(L.Dop, L.O, L.cs, L.co_t, mesh->nbr, mesh->d, x, y, L.nb, mesh->E, st);
+  return launch_bsr<T>(L.Dop, L.O, L.cs, L.co_t, mesh->face_nbr(), mesh->nfaces(), x, y, L.nb, mesh->E, st);
 }
 
 // SMOOTH / SOLVE: nu iterations of GMRES right-preconditioned by block Jacobi
@@ -204,13 +204,14 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
       // probe_nbr_kernel (decided here once: the captured graph relies on it)
       // (the column-major mat-vec runs one thread per block and 16 bytes of rows: at most 256 per element)
       const int tpb1 = (1 + 2 * M.d) * (inv_ld<T>(mg.lv[1].nb) / (int)(16 / sizeof(T)));
-      L.co_t = std::is_same<T, float>::value && tpb1 <= 256 && probe_nbr_colmajor_ok(M, mg.lv[1].nm) ? 1 : 0;
+      L.co_t = M.kind == DG_MESH_STRUCTURED && std::is_same<T, float>::value && tpb1 <= 256 &&
+                       probe_nbr_colmajor_ok(M, mg.lv[1].nm) ? 1 : 0;
       L.cs = L.co_t ? L.bs : (size_t)L.nb * L.nb;
       (void)nbl;
       CK(dalloc(mg.allocs, (void**)&L.Dop, sizeof(T) * (size_t)M.E * L.cs, &h->block_bytes));
-      CK(dalloc(mg.allocs, (void**)&L.O, sizeof(T) * (size_t)M.E * 2 * M.d * L.cs, &h->block_bytes));
+      CK(dalloc(mg.allocs, (void**)&L.O, sizeof(T) * (size_t)M.E * M.nfaces() * L.cs, &h->block_bytes));
       CK(cudaMemset(L.Dop, 0, sizeof(T) * (size_t)M.E * L.cs));   // padding rows stay zero
-      CK(cudaMemset(L.O, 0, sizeof(T) * (size_t)M.E * 2 * M.d * L.cs));
+      CK(cudaMemset(L.O, 0, sizeof(T) * (size_t)M.E * M.nfaces() * L.cs));
     }
     for (T** v : {&L.x, &L.b, &L.r, &L.t}) CK(dalloc(mg.allocs, (void**)v, sizeof(T) * L.N, &h->vector_bytes));
     int nmax = (l == nl - 1) ? std::max(1, o.nu_coarse) : std::max(std::max(L.nu_pre, L.nu_post), 1);
@@ -222,7 +223,8 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
   // primal traces of the fine JVP's linearisation point (FP32 smoother JVPs);
   // DG_PMG_NO_PRIMAL_CACHE=1 makes every JVP interpolate W itself
   const char* npc = getenv("DG_PMG_NO_PRIMAL_CACHE");
-  if (std::is_same<T, float>::value && !(npc && npc[0] == '1') && o.cycle != DG_CYCLE_BJ) {
+  if (M.kind == DG_MESH_STRUCTURED && std::is_same<T, float>::value && !(npc && npc[0] == '1') &&
+      o.cycle != DG_CYCLE_BJ) {
     size_t nf = 0, nv = primal_cache_sizes(M, &nf);
     CK(dalloc(mg.allocs, (void**)&mg.Pv, sizeof(T) * nv, &h->vector_bytes));
     CK(dalloc(mg.allocs, (void**)&mg.Pf, sizeof(T) * nf, &h->vector_bytes));
@@ -251,7 +253,7 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
   }
   // probing caches live in global memory when they exceed shared memory
   bool fits = true;
-  size_t tot = probe_scratch_elems<T>(M, nl > 1 ? mg.lv[1].nm : 0, &fits);
+  size_t tot = M.kind == DG_MESH_STRUCTURED ? probe_scratch_elems<T>(M, nl > 1 ? mg.lv[1].nm : 0, &fits) : 0;
   if (!fits) {
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
@@ -276,9 +278,13 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
   else
     CK(launch_convert<double, float>(N0, W64, (float*)mg.W, st));
   if (mg.Pv) CK(launch_primal_cache(M, (const float*)mg.W, (float*)mg.Pv, (float*)mg.Pf, st));
-  CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, mg.lv[0].bs, nl > 1 ? mg.lv[1].O : nullptr,
-                            nl > 1 ? mg.lv[1].nm : 0, nl > 1 ? mg.lv[1].co_t : 0, mg.scratch, mg.scratch_elems,
-                            st));
+  if (M.kind == DG_MESH_TRI)   // coloured JVP probing, seeds and products in level 0's work vectors
+    CK(launch_probe_blocks_tri<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, mg.lv[0].bs, nl > 1 ? mg.lv[1].O : nullptr,
+                                  nl > 1 ? mg.lv[1].nm : 0, mg.lv[0].r, mg.lv[0].t, st));
+  else
+    CK(launch_probe_blocks<T>(M, mg.W, (T)h->sigma, mg.lv[0].Dinv, mg.lv[0].bs, nl > 1 ? mg.lv[1].O : nullptr,
+                              nl > 1 ? mg.lv[1].nm : 0, nl > 1 ? mg.lv[1].co_t : 0, mg.scratch, mg.scratch_elems,
+                              st));
   const Level<T>& F = mg.lv[0];
   for (int l = 1; l < nl; ++l) {
     Level<T>& L = mg.lv[l];
@@ -288,7 +294,7 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
     CK(launch_truncate_blocks<T>(F.Dinv, F.nm, F.bs, 0, L.Dinv, L.nm, L.bs, 0, M.m, M.E, st));
     if (l >= 2)
       CK(launch_truncate_blocks<T>(mg.lv[1].O, mg.lv[1].nm, mg.lv[1].cs, mg.lv[1].co_t, L.O, L.nm, L.cs, L.co_t,
-                                   M.m, (long)M.E * 2 * M.d, st));
+                                   M.m, (long)M.E * M.nfaces(), st));
   }
   for (int l = 0; l < nl; ++l)
     CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, mg.lv[l].bs, M.E, M.status, &mg.lv[l].inv_t, st));
@@ -381,7 +387,6 @@ static dg_status capture_apply_graph(dg_pmg h) {
 }
 
 static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
-  if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;   // blocks of structured meshes only
   if (o->cycle != DG_CYCLE_FMG && o->cycle != DG_CYCLE_V && o->cycle != DG_CYCLE_BJ) return DG_ERR_INVALID;
   if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
   if (o->fgmres_restart < 0 || o->fgmres_restart > 64) return DG_ERR_INVALID;
@@ -391,6 +396,7 @@ static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
     // needs a face graph without triangles (no periodic direction of 3)
     if (o->cycle == DG_CYCLE_BJ || o->n_levels < 2) return DG_ERR_INVALID;
     if (o->coarse_order < DG_ORDER_MDF || o->coarse_order > DG_ORDER_COLOUR) return DG_ERR_INVALID;
+    if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;
     for (int k = 0; k < mesh->m.d; ++k)
       if (mesh->m.desc.n[k] == 3) return DG_ERR_INVALID;
   }
@@ -544,7 +550,7 @@ static dg_status export_level(const MG<T>& mg, const Mesh& M, T* W, double sigma
                               size_t out_bytes, cudaStream_t st) {
   const Level<T>& L = mg.lv[level];
   const int nb = L.nb;
-  const size_t nblk = which == DG_BLOCKS_NEIGHBOUR ? (size_t)M.E * 2 * M.d : (size_t)M.E;
+  const size_t nblk = which == DG_BLOCKS_NEIGHBOUR ? (size_t)M.E * M.nfaces() : (size_t)M.E;
   if (out_bytes < nblk * nb * nb * sizeof(T)) return DG_ERR_INVALID;
   if (which == DG_BLOCKS_DIAG_INV) {
     CK(launch_unpack_inverse<T>(L.Dinv, L.bs, L.inv_t, out, nb, (long)nblk, st));
@@ -552,7 +558,9 @@ static dg_status export_level(const MG<T>& mg, const Mesh& M, T* W, double sigma
     if (level < 1) return DG_ERR_INVALID;
     CK(launch_unpack_inverse<T>(L.O, L.cs, L.co_t, out, nb, (long)nblk, st));
   } else if (which == DG_BLOCKS_DIAG) {
-    if (level == 0)   // the fine-level probe again, at the stored state and shift
+    if (level == 0 && M.kind == DG_MESH_TRI)   // the fine-level probe again, at the stored state and shift
+      CK(launch_probe_blocks_tri<T>(M, W, (T)sigma, out, (size_t)nb * nb, nullptr, 0, mg.lv[0].r, mg.lv[0].t, st));
+    else if (level == 0)
       CK(launch_probe_blocks<T>(M, W, (T)sigma, out, (size_t)nb * nb, nullptr, 0, 0, mg.scratch, mg.scratch_elems,
                                 st));
     else
@@ -675,35 +683,44 @@ unsigned long long& launch_counter() {
   return n;
 }
 
+// c = |J|/(2 dt); with geo (triangles: [E][5], |J| at 4) c is 1/(2 dt) and |J| per element
 __global__ void bdf2_rhs_kernel(long N, const double* __restrict__ Wk, const double* __restrict__ Wn,
-                                const double* __restrict__ Wnm1, double c, double* __restrict__ b) {
+                                const double* __restrict__ Wnm1, double c, const double* __restrict__ geo, int nb,
+                                double* __restrict__ b) {
   // on entry b holds R(Wk)
-  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
-    b[n] = -(c * (3.0 * Wk[n] - 4.0 * Wn[n] + Wnm1[n]) + b[n]);
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    const double ce = geo ? c * geo[(n / nb) * 5 + 4] : c;
+    b[n] = -(ce * (3.0 * Wk[n] - 4.0 * Wn[n] + Wnm1[n]) + b[n]);
+  }
 }
 }  // namespace dgk
 
 extern "C" dg_status dg_bdf2_rhs(dg_mesh mesh, const double* Wk, const double* Wn, const double* Wnm1, double dt,
                                  double* b, void* stream) {
   if (!mesh || !Wk || !Wn || !Wnm1 || !b || b == Wk || b == Wn || b == Wnm1 || !(dt > 0.0)) return DG_ERR_INVALID;
-  if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;   // one |J| per mesh
   cudaStream_t st = (cudaStream_t)stream;
   const Mesh& M = mesh->m;
   const long N = (long)M.E * M.nb;
   CK(launch_residual<double>(M, Wk, nullptr, nullptr, 0.0, false, b, st));
   int gr = (int)std::min<long>((N + 255) / 256, 4096);
   note_launch();
-  bdf2_rhs_kernel<<<gr, 256, 0, st>>>(N, Wk, Wn, Wnm1, M.detJ / (2.0 * dt), b);
+  const bool tri = M.kind == DG_MESH_TRI;
+  bdf2_rhs_kernel<<<gr, 256, 0, st>>>(N, Wk, Wn, Wnm1, (tri ? 1.0 : M.detJ) / (2.0 * dt), tri ? M.tr64.geo : nullptr,
+                                      M.nb, b);
   CK(cudaGetLastError());
   return DG_OK;
 }
 
 namespace dgk {
 // b = -(c (Wk - Wn) + racc + b), b holding R(Wk) on entry; racc may be null
+// c = sigma |J|, or sigma with |J| per element from geo (triangles)
 __global__ void esdirk_rhs_kernel(long N, const double* __restrict__ Wk, const double* __restrict__ Wn,
-                                  const double* __restrict__ racc, double c, double* __restrict__ b) {
-  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
-    b[n] = -(c * (Wk[n] - Wn[n]) + (racc ? racc[n] : 0.0) + b[n]);
+                                  const double* __restrict__ racc, double c, const double* __restrict__ geo, int nb,
+                                  double* __restrict__ b) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    const double ce = geo ? c * geo[(n / nb) * 5 + 4] : c;
+    b[n] = -(ce * (Wk[n] - Wn[n]) + (racc ? racc[n] : 0.0) + b[n]);
+  }
 }
 
 // ESDIRK3 (four stages, third order, explicit first stage, stiffly accurate):
@@ -720,14 +737,15 @@ constexpr double ES_A[4][4] = {
 extern "C" dg_status dg_esdirk3_rhs(dg_mesh mesh, const double* Wk, const double* Wn, double sigma,
                                     const double* racc, double* b, void* stream) {
   if (!mesh || !Wk || !Wn || !b || b == Wk || b == Wn || b == racc || !(sigma > 0.0)) return DG_ERR_INVALID;
-  if (mesh->m.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;   // one |J| per mesh
   cudaStream_t st = (cudaStream_t)stream;
   const Mesh& M = mesh->m;
   const long N = (long)M.E * M.nb;
   CK(launch_residual<double>(M, Wk, nullptr, nullptr, 0.0, false, b, st));
   int gr = (int)std::min<long>((N + 255) / 256, 4096);
   note_launch();
-  esdirk_rhs_kernel<<<gr, 256, 0, st>>>(N, Wk, Wn, racc, sigma * M.detJ, b);
+  const bool tri = M.kind == DG_MESH_TRI;
+  esdirk_rhs_kernel<<<gr, 256, 0, st>>>(N, Wk, Wn, racc, sigma * (tri ? 1.0 : M.detJ), tri ? M.tr64.geo : nullptr,
+                                        M.nb, b);
   CK(cudaGetLastError());
   return DG_OK;
 }

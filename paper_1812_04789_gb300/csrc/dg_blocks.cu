@@ -640,25 +640,25 @@ __global__ void __launch_bounds__(256) bsr_colmajor_kernel(const T* __restrict__
 }
 
 template <class T>
-cudaError_t launch_bsr(const T* D, const T* O, size_t bstride, int transposed, const int* nbr, int d, const T* x,
+cudaError_t launch_bsr(const T* D, const T* O, size_t bstride, int transposed, const int* nbr, int nf, const T* x,
                        T* y, int nb, int E, cudaStream_t st) {
   if (transposed) {
-    const int ld = inv_ld<T>(nb), tpe = ld / Vec16<T>::N, tpb = (1 + 2 * d) * tpe;
+    const int ld = inv_ld<T>(nb), tpe = ld / Vec16<T>::N, tpb = (1 + nf) * tpe;
     if (tpb <= 256) {
       const int epc = std::max(1, 256 / tpb);
       const int threads = (epc * tpb + 31) / 32 * 32;
       const int grid = std::min((E + epc - 1) / epc, 16 * num_sms());
-      const size_t smem = (size_t)epc * (1 + 2 * d) * (nb + ld) * sizeof(T);
+      const size_t smem = (size_t)epc * (1 + nf) * (nb + ld) * sizeof(T);
       note_launch();
-      bsr_colmajor_kernel<T><<<grid, threads, smem, st>>>(D, O, bstride, nbr, 2 * d, x, y, nb, ld, E, epc, tpe);
+      bsr_colmajor_kernel<T><<<grid, threads, smem, st>>>(D, O, bstride, nbr, nf, x, y, nb, ld, E, epc, tpe);
       return cudaGetLastError();
     }
     return cudaErrorInvalidValue;   // coarse blocks this large are stored row-major
   }
   int grid = std::min(E, 32 * num_sms());
-  size_t smem = (size_t)(1 + 2 * d) * nb * sizeof(T);
+  size_t smem = (size_t)(1 + nf) * nb * sizeof(T);
   note_launch();
-  bsr_kernel<T><<<grid, 256, smem, st>>>(D, bstride, O, nbr, 2 * d, x, y, nb, E);
+  bsr_kernel<T><<<grid, 256, smem, st>>>(D, bstride, O, nbr, nf, x, y, nb, E);
   return cudaGetLastError();
 }
 template cudaError_t launch_bsr<double>(const double*, const double*, size_t, int, const int*, int, const double*,

@@ -88,6 +88,10 @@ struct Mesh {
   int* tnbrf = nullptr;      //   and that neighbour's local edge
   TriTab<double> tr64;
   TriTab<float> tr32;
+  int* tcolour = nullptr;    // triangles: device [E] greedy colouring (no two neighbours alike)
+  int tncol = 0;
+  int nfaces() const { return kind == DG_MESH_TRI ? 3 : 2 * d; }
+  const int* face_nbr() const { return kind == DG_MESH_TRI ? tnbr : nbr; }   // [E][nfaces]
   int* status = nullptr;     // device status word
   double* scal = nullptr;    // device scalars for the FD JVP (norms, h)
   double* partials = nullptr;// reduction partials for the FD JVP norms
@@ -105,6 +109,12 @@ template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
                             T* out, cudaStream_t st, const T* Pv = nullptr, const T* Pf = nullptr);
 
+// Blocks of a triangle mesh by coloured JVP probing (csrc/dg_tri.cu): D (row-
+// major, dstride apart) = dR_e/dW_e + sigma |J_e| I; O (if given, row-major
+// nbc^2 apart, [E][3]) the neighbour blocks on the modes of the first nmc.
+template <class T>
+cudaError_t launch_probe_blocks_tri(const Mesh& M, const T* W, T sigma, T* D, size_t dstride, T* O, int nmc,
+                                    T* seed, T* out, cudaStream_t st);
 // Residual / exact JVP on a triangle mesh (csrc/dg_tri.cu), same contract.
 template <class T>
 cudaError_t launch_residual_tri(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,

@@ -435,6 +435,76 @@ template cudaError_t launch_residual_tri<double>(const Mesh&, const double*, con
 template cudaError_t launch_residual_tri<float>(const Mesh&, const float*, const float*, const float*, float, bool,
                                                 float*, cudaStream_t);
 
+// ---------------------------------------------------------------- blocks
+// Block probing by coloured JVPs (Sec. 5.1 blocks of the iteration matrix):
+// the seed is the unit direction jj on every triangle of colour c.  No two
+// triangles of one colour are neighbours, so the JVP's rows on colour c are
+// column jj of D_e = dR_e/dW_e + sigma |J_e| I, and the face slot of edge f of
+// a triangle whose neighbour across f has colour c is column jj of the
+// neighbour block (that slot depends on the two triangles only).
+namespace {
+
+template <class T>
+__global__ void tri_seed_kernel(long N, int nb, const int* __restrict__ colour, int c, int jj, T* __restrict__ seed) {
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    const long e = n / nb;
+    seed[n] = (colour[e] == c && n - e * nb == jj) ? T(1) : T(0);
+  }
+}
+
+template <class T>
+__global__ void tri_gather_kernel(int E, int nb, int nm, const int* __restrict__ colour, const int* __restrict__ nbr,
+                                  int c, int jj, const T* __restrict__ out, const T* __restrict__ slots, T* D,
+                                  size_t dstride, T* O, int nmc) {
+  const int nbc = 4 * nmc;
+  const long nD = (long)E * nb, nO = O ? (long)E * 3 * nbc : 0;
+  const int jv = jj / nm, ji = jj - jv * nm;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nD + nO; t += (long)gridDim.x * blockDim.x) {
+    if (t < nD) {
+      const long e = t / nb;
+      const int r = (int)(t - e * nb);
+      if (colour[e] == c) D[e * dstride + (size_t)r * nb + jj] = out[t];
+    } else {
+      const long t2 = t - nD, ef = t2 / nbc;   // ef = 3 e + f
+      const int rc = (int)(t2 - ef * nbc);
+      const long e = ef / 3;
+      const int k = nbr[ef];
+      if (ji < nmc && k != e && colour[k] == c) {
+        const int rv = rc / nmc, ri = rc - rv * nmc;
+        O[ef * nbc * nbc + (size_t)rc * nbc + jv * nmc + ji] = slots[ef * nb + rv * nm + ri];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_probe_blocks_tri(const Mesh& M, const T* W, T sigma, T* D, size_t dstride, T* O, int nmc,
+                                    T* seed, T* out, cudaStream_t st) {
+  const long N = (long)M.E * M.nb;
+  const T* slots = std::is_same<T, double>::value ? (const T*)M.t64.slots : (const T*)M.t32.slots;
+  const int gs = (int)std::min<long>((N + 255) / 256, 4096);
+  const long ng = N + (O ? (long)M.E * 3 * 4 * nmc : 0);
+  const int gg = (int)std::min<long>((ng + 255) / 256, 4096);
+  for (int c = 0; c < M.tncol; ++c)
+    for (int jj = 0; jj < M.nb; ++jj) {
+      note_launch();
+      tri_seed_kernel<T><<<gs, 256, 0, st>>>(N, M.nb, M.tcolour, c, jj, seed);
+      cudaError_t e = launch_residual_tri<T>(M, W, seed, nullptr, sigma, true, out, st);
+      if (e != cudaSuccess) return e;
+      note_launch();
+      tri_gather_kernel<T><<<gg, 256, 0, st>>>(M.E, M.nb, M.nm, M.tcolour, M.tnbr, c, jj, out, slots, D, dstride, O,
+                                               nmc);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+template cudaError_t launch_probe_blocks_tri<double>(const Mesh&, const double*, double, double*, size_t, double*, int,
+                                                     double*, double*, cudaStream_t);
+template cudaError_t launch_probe_blocks_tri<float>(const Mesh&, const float*, float, float*, size_t, float*, int,
+                                                    float*, float*, cudaStream_t);
+
 // ---------------------------------------------------------------- mesh build
 namespace {
 
@@ -583,6 +653,25 @@ dg_status build_tri(Mesh& M, const dg_tri_desc* d, const dg_physics* ph) {
   if (cudaMemcpy(M.tnbr, nbr.data(), sizeof(int) * E * 3, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(M.tnbrf, nbrf.data(), sizeof(int) * E * 3, cudaMemcpyHostToDevice) != cudaSuccess)
     return DG_ERR_CUDA;
+  // greedy colouring in index order (no two face neighbours share a colour)
+  std::vector<int> col(E, 0);
+  M.tncol = 0;
+  for (int e = 0; e < E; ++e) {
+    int c = 0;
+    for (bool clash = true; clash; ) {
+      clash = false;
+      for (int f = 0; f < 3; ++f) {
+        const int k = nbr[(size_t)e * 3 + f];
+        if (k < e && col[k] == c) clash = true;
+      }
+      if (clash) ++c;
+    }
+    col[e] = c;
+    M.tncol = std::max(M.tncol, c + 1);
+  }
+  if (cudaMalloc((void**)&M.tcolour, sizeof(int) * E) != cudaSuccess) return DG_ERR_OOM;
+  M.allocs.push_back(M.tcolour);
+  if (cudaMemcpy(M.tcolour, col.data(), sizeof(int) * E, cudaMemcpyHostToDevice) != cudaSuccess) return DG_ERR_CUDA;
   if (alloc_scratch<double>(M, M.t64) != cudaSuccess || alloc_scratch<float>(M, M.t32) != cudaSuccess)
     return DG_ERR_OOM;
   if (cudaMalloc((void**)&M.status, sizeof(int)) != cudaSuccess) return DG_ERR_OOM;

@@ -1,9 +1,12 @@
-"""Triangle meshes through the C ABI (dg_mesh_create_tri): residual and exact
-JVP against the oracle's triangular DG (Sec. 3: full-order P_p on triangles).
+"""Triangle meshes through the C ABI (dg_mesh_create_tri): residual, exact
+JVP, blocks, p-multigrid and a BDF2 Newton update against the oracle's
+triangular DG (Sec. 3: full-order P_p on triangles).
 
-Bars: FP64 residual and JVP 1e-12 in the relative max-norm (the quadrature
-sums of the oracle in another order), FP32 JVP mode 2e-5; free stream to
-rounding; discrete conservation; invalid meshes rejected."""
+Bars: FP64 residual, JVP and blocks 1e-12 in the relative max-norm (the
+quadrature sums of the oracle in another order), FP32 JVP mode 2e-5; pMG
+apply 1e-10; FGMRES (FP64) iterations +-1 and 1e-10, mixed 10 % + 1 and
+1e-6; free stream to rounding; discrete conservation; invalid meshes and
+unsupported calls rejected."""
 import math
 
 import numpy as np
@@ -114,8 +117,84 @@ def test_invalid_triangulations_and_unsupported_calls():
         B.Mesh.from_tri_workload(open_, P, 2)
     gm = B.Mesh.from_tri_workload(msh, P, 2)
     W = dev(wl.tri_initial_state(cfg))
-    with pytest.raises(B.DGError):
-        B.PMG(gm, W, 1.0, B.pmg_opts((2,), cycle=B.CYCLE_BJ))
-    b = torch.empty_like(W)
-    with pytest.raises(B.DGError):
-        gm.bdf2_rhs(W, W, W, 0.1, b)
+    with pytest.raises(B.DGError):                 # block ILU(0): structured meshes only
+        B.PMG(gm, W, 1.0, B.pmg_opts((2, 1), coarse=B.COARSE_BILU))
+    Kv = torch.empty_like(W)
+    with pytest.raises(B.DGError):                 # the FD JVP: structured meshes only
+        gm.jvp(W, W, Kv, 1.0, mode=B.JVP_FD, R_W=Kv.clone())
+
+
+def _levels_case():
+    cfg = wl.tri_config((4, 3), 2, p_levels=(2, 1, 0))
+    om, oph, gm = both(cfg)
+    W = wl.tri_perturbed_state(cfg, amp=0.05)
+    sigma = 1.5 / wl.time_step(cfg)
+    return cfg, om, oph, gm, W, sigma
+
+
+def test_blocks_parity():
+    """Coloured JVP probing: diagonal blocks (level 0) and neighbour blocks
+    (level 1) against the oracle's complex-step probing."""
+    cfg, om, oph, gm, W, sigma = _levels_case()
+    pmg = B.PMG(gm, dev(W), sigma, B.pmg_opts((2, 1, 0), nu_pre=3, nu_post=3, nu_coarse=5))
+    nb, nbc = 4 * om.nm, 4 * otri.n_modes_tri(1)
+    D = torch.empty((om.E, nb, nb), dtype=torch.float64, device="cuda")
+    pmg.export_blocks(0, B.BLOCKS_DIAG, D)
+    Dref = otri.diag_blocks(om, oph, W, sigma)
+    assert relmax(D.cpu().numpy(), Dref) <= 1e-12
+    O = torch.empty((om.E, 3, nbc, nbc), dtype=torch.float64, device="cuda")
+    pmg.export_blocks(1, B.BLOCKS_NEIGHBOUR, O)
+    Oref = otri.offdiag_blocks(om, oph, W, 1)
+    assert relmax(O.cpu().numpy(), Oref) <= 1e-12
+
+
+@pytest.mark.parametrize("cycle", [B.CYCLE_FMG, B.CYCLE_V, B.CYCLE_BJ])
+def test_pmg_apply_parity(cycle):
+    cfg, om, oph, gm, W, sigma = _levels_case()
+    pl, nu, nuc = (2, 1, 0), 3, 5
+    mg = otri.pmg_setup(om, oph, W, sigma, pl, nu_pre=nu, nu_post=nu, nu_coarse=nuc)
+    r = wl.random_vector(W.shape, 21)
+    ref = mg.mg_full(r) if cycle == B.CYCLE_FMG else (mg.mg_v(0, r, np.zeros_like(r)) if cycle == B.CYCLE_V
+                                                      else mg.P[0](r))
+    pmg = B.PMG(gm, dev(W), sigma, B.pmg_opts(pl, nu_pre=nu, nu_post=nu, nu_coarse=nuc, cycle=cycle))
+    z = torch.empty(W.shape, dtype=torch.float64, device="cuda")
+    pmg.apply(dev(r), z)
+    assert gm.status_sync() == B.DG_OK
+    err = relmax(z.cpu().numpy(), ref)
+    print("triangles, cycle %d: pMG apply rel max err %.3e" % (cycle, err))
+    assert err <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [B.PREC_FP64, B.PREC_MIXED])
+def test_bdf2_fgmres_step(precision):
+    """One BDF2 Newton update (W^{n-1} = W^n) with FGMRES(pMG) on triangles:
+    the right-hand side with the per-triangle mass, iterations and the state
+    against the oracle (FP64: +-1 and 1e-10; mixed: 10 % + 1 and 1e-6)."""
+    cfg, om, oph, gm, W, sigma = _levels_case()
+    from oracle.solvers import fgmres
+    dt = wl.time_step(cfg)
+    bref = -otri.residual(om, oph, W)
+    b = torch.empty(W.shape, dtype=torch.float64, device="cuda")
+    gm.bdf2_rhs(dev(W), dev(W), dev(W), dt, b)
+    assert relmax(b.cpu().numpy(), bref) <= 1e-12
+    Wk = W + 0.01 * wl.random_vector(W.shape, 3) * np.abs(W).max()
+    bref = -(otri.mass_apply(om, 3.0 * Wk - 4.0 * W + W) / (2.0 * dt) + otri.residual(om, oph, Wk))
+    gm.bdf2_rhs(dev(Wk), dev(W), dev(W), dt, b)
+    assert relmax(b.cpu().numpy(), bref) <= 1e-12
+    pl, nu, nuc = (2, 1, 0), 4, 8
+    mg = otri.pmg_setup(om, oph, W, sigma, pl, nu_pre=nu, nu_post=nu, nu_coarse=nuc)
+    rhs = -otri.residual(om, oph, W)
+    x_ref, st_ref = fgmres(lambda z: otri.jvp(om, oph, W, z, sigma), mg, rhs, restart=30, rtol=1e-5, max_restarts=3)
+    pmg = B.PMG(gm, dev(W), sigma, B.pmg_opts(pl, nu_pre=nu, nu_post=nu, nu_coarse=nuc, precision=precision))
+    dW = torch.empty(W.shape, dtype=torch.float64, device="cuda")
+    st = pmg.fgmres(dev(W), dev(rhs), dW, rtol=1e-5, max_restarts=3)
+    x = dW.cpu().numpy()
+    rel = np.linalg.norm(x - x_ref) / np.linalg.norm(W + x_ref)
+    print("triangles, precision %d: FGMRES %d iterations vs oracle %d, rel %.3e" % (precision, st["iters"],
+                                                                                     st_ref["iters"], rel))
+    if precision == B.PREC_FP64:
+        assert abs(st["iters"] - st_ref["iters"]) <= 1 and rel <= 1e-10
+    else:
+        assert st["iters"] <= int(1.1 * st_ref["iters"]) + 1 and rel <= 1e-6
+    res = rhs - otri.jvp(om, oph, W, x, sigma)
+    assert np.linalg.norm(res) <= 1.0001e-5 * np.linalg.norm(rhs)
