@@ -101,9 +101,12 @@ dg_status dg_mesh_destroy(dg_mesh mesh);
  * (-1,1), ordered by total degree i + j, then i descending; state layout
  * W[e][v][i] as for dg_mesh_create; nq1d (0 => p + 2) points per direction of
  * the collapsed Gauss rule and per edge; the BR2 penalty eta_br2 = 0 means 4
- * (n_faces + 1).  Such a handle serves dg_residual, dg_jvp (exact modes),
- * dg_mesh_info and dg_status_sync; the p-multigrid, the BDF2 / ESDIRK3
- * right-hand sides, the FD JVP and dg_residual_noalloc return DG_ERR_INVALID.
+ * (n_faces + 1).  Such a handle serves dg_residual, dg_jvp (exact modes), the
+ * p-multigrid (blocks by coloured JVP probing, three neighbour blocks per
+ * triangle; block Jacobi smoothers), dg_fgmres_step, the BDF2 / ESDIRK3
+ * right-hand sides and steps (per-triangle mass |J_e|), dg_mesh_info and
+ * dg_status_sync; the FD JVP modes, the block ILU(0) coarse option and
+ * dg_residual_noalloc return DG_ERR_INVALID.
  * DG_ERR_INVALID on bad sizes, indices, a clockwise or degenerate triangle or
  * an edge not shared by exactly two triangles. */
 typedef struct {
