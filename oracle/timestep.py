@@ -31,7 +31,8 @@ def esdirk3_step(R, solve, Wn, dt, mass, newton=2):
 
     R(W): residual; solve(Wk, sigma, f) returns dW with K(Wk) dW = -f,
     K = sigma mass + dR/dW(Wk), sigma = 1 / (a_ii dt) (the same for every
-    implicit stage); mass: the scalar |J| of M = |J| I (or 1 for an ODE).
+    implicit stage); mass: |J| of M = |J| I, a scalar or an array broadcast
+    against W (one |J| per element), or 1 for an ODE.
     Each implicit stage starts from the previous stage's value and takes
     `newton` Newton iterations (eq. NEWTON); R of stages 1..3 is kept for the
     sums of the later stages."""
@@ -52,9 +53,14 @@ def esdirk3_dg_step(mesh, ph, Wn, dt, P, newton=2, rtol=1e-5, max_restarts=4):
     """ESDIRK3 step of the DG system with FGMRES (exact JVP) preconditioned by
     P, assembled once at W^n with sigma = 1/(a_ii dt) and reused for every stage
     and Newton iteration (Sec. 7.4, "MFL").  Returns (W^{n+1}, FGMRES iteration
-    counts per solve)."""
-    from .dg import residual, jvp
+    counts per solve).  A triangle mesh (``oracle.tri.TriMesh``) takes its own
+    residual, JVP and per-triangle mass |J_e|."""
+    from . import dg, tri
     from .solvers import fgmres
+    if isinstance(mesh, tri.TriMesh):
+        residual, jvp, mass = tri.residual, tri.jvp, mesh.detJ[:, None, None]
+    else:
+        residual, jvp, mass = dg.residual, dg.jvp, mesh.detJ
     its = []
 
     def solve(Wk, sigma, f):
@@ -62,5 +68,5 @@ def esdirk3_dg_step(mesh, ph, Wn, dt, P, newton=2, rtol=1e-5, max_restarts=4):
         its.append(st["iters"])
         return x
 
-    W1 = esdirk3_step(lambda W: residual(mesh, ph, W), solve, Wn, dt, mesh.detJ, newton)
+    W1 = esdirk3_step(lambda W: residual(mesh, ph, W), solve, Wn, dt, mass, newton)
     return W1, its

@@ -238,3 +238,29 @@ def test_blocks_rebuild_the_jvp_and_pmg_converges():
     assert st_bj["converged"] and st_mg["converged"]
     assert st_mg["iters"] < st_bj["iters"]
     assert np.linalg.norm(b - K(x)) <= 1.0001e-8 * np.linalg.norm(b)
+
+
+def test_esdirk3_step_on_triangles():
+    """The ESDIRK3 step (Sec. 4) with the per-triangle mass: a uniform state
+    stays put, and on the vortex successive halvings of the step change the
+    state by amounts that shrink ~8x (third order)."""
+    from oracle import timestep as ts
+    cfg = wl.tri_config((3, 3), 1, Re=1.0e4)
+    M, ph = tri_mesh(cfg), tri_phys(cfg)
+    W = uniform(cfg)
+    dt = wl.time_step(cfg)
+    P = BlockJacobi(tri.diag_blocks(M, ph, W, 1.0 / (ts.GAMMA * dt)), 4, M.nm)
+    W1, _ = ts.esdirk3_dg_step(M, ph, W, dt, P, newton=1)
+    assert np.abs(W1 - W).max() <= 1e-12 * np.abs(W).max()
+    W0 = wl.tri_initial_state(cfg)
+
+    def run(h, n):
+        Wc = W0.copy()
+        Pc = BlockJacobi(tri.diag_blocks(M, ph, Wc, 1.0 / (ts.GAMMA * h)), 4, M.nm)   # lagged: any P converges
+        for _ in range(n):
+            Wc, _ = ts.esdirk3_dg_step(M, ph, Wc, h, Pc, newton=3, rtol=1e-12, max_restarts=8)
+        return Wc
+    T = 0.4
+    w1, w2, w4 = run(T, 1), run(T / 2, 2), run(T / 4, 4)
+    d1, d2 = np.abs(w1 - w2).max(), np.abs(w2 - w4).max()
+    assert d1 / d2 > 5.0, (d1, d2)
