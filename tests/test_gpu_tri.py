@@ -198,3 +198,26 @@ def test_bdf2_fgmres_step(precision):
         assert st["iters"] <= int(1.1 * st_ref["iters"]) + 1 and rel <= 1e-6
     res = rhs - otri.jvp(om, oph, W, x, sigma)
     assert np.linalg.norm(res) <= 1.0001e-5 * np.linalg.norm(rhs)
+
+
+def test_esdirk3_step_on_triangles():
+    """dg_esdirk3_step on a triangle handle (per-triangle mass in the stage
+    right-hand sides) against the oracle's ESDIRK3 step: FP64, W^{n+1} within
+    1e-10 relative L2, FGMRES iterations within one per solve."""
+    from oracle import timestep as ots
+    cfg, om, oph, gm, W, _ = _levels_case()
+    dt = wl.time_step(cfg)
+    sigma = 1.0 / (ots.GAMMA * dt)
+    pl, nu, nuc, newton = (2, 1, 0), 4, 8, 2
+    P = otri.pmg_setup(om, oph, W, sigma, pl, nu_pre=nu, nu_post=nu, nu_coarse=nuc)
+    W1_ref, its = ots.esdirk3_dg_step(om, oph, W, dt, P, newton=newton, rtol=1e-5, max_restarts=3)
+    pmg = B.PMG(gm, dev(W), sigma, B.pmg_opts(pl, nu_pre=nu, nu_post=nu, nu_coarse=nuc))
+    Wout = torch.empty(W.shape, dtype=torch.float64, device="cuda")
+    st = pmg.esdirk3_step(dev(W), dt, Wout, newton=newton, max_restarts=3)
+    assert gm.status_sync() == B.DG_OK
+    W1 = Wout.cpu().numpy()
+    rel = np.linalg.norm(W1 - W1_ref) / np.linalg.norm(W1_ref)
+    print("triangles: ESDIRK3 step rel L2 %.3e, iterations %d vs oracle %d" % (rel, st["iters"], sum(its)))
+    assert abs(st["iters"] - sum(its)) <= 3 * newton
+    assert rel <= 1e-10
+    assert np.linalg.norm(W1 - W) / np.linalg.norm(W) > 1e-8     # the step moved the state
