@@ -150,10 +150,40 @@ class Stepper:
         return self.Wk
 
 
+# ---------------------------------------------------------------- ranks
+def dist_on():
+    import torch.distributed as dist
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def dist_barrier():
+    """Barrier across the ranks of a torchrun launch (no-op for one process)."""
+    if dist_on():
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, device):
+    """The largest of every rank's value (each rank's timed seconds)."""
+    if not dist_on():
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
+
+
 def timed_steps(torch, stepper, steps, warmup, newton, stream, flush):
     for _ in range(warmup):
         stepper.step(newton)
     torch.cuda.synchronize()
+    dist_barrier()                          # every rank starts the timed steps together
     times = []
     stepper.iters.clear()
     for _ in range(steps):
@@ -166,6 +196,8 @@ def timed_steps(torch, stepper, steps, warmup, newton, stream, flush):
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    dist_barrier()
     return times
 
 
@@ -507,12 +539,8 @@ def run_gb300(args):
             if name == "mixed":
                 launches = B.launch_count() - l0
                 clk = clocks.stop()
-            tot = sum(times) / 1e3
-            if world > 1:
-                t = torch.tensor([tot], device="cuda", dtype=torch.float64)
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                tot = float(t.item())
-            results[name] = dict(ms_per_step=1e3 * tot / steps, value=world * st.ndofs * steps / tot,
+            tot = max_over_ranks(sum(times) / 1e3, "cuda")
+            results[name] = dict(ms_per_step=1e3 * tot / steps, value=whole_job_rate(world, st.ndofs, steps, tot),
                                  fgmres_iters_per_solve=statistics.mean(st.iters), ndofs=st.ndofs,
                                  Wfinal=st.Wk.cpu().numpy() if name in ("mixed", "fp64") else None)
             if name == "mixed":
