@@ -46,7 +46,7 @@ typedef enum {
   DG_ERR_NOT_CONVERGED = 5,  /* FGMRES stopped at its iteration limit above tolerance */
   DG_ERR_BREAKDOWN = 6,      /* singular element block, or non-finite Krylov scalar */
   DG_ERR_TIMEOUT = 7,        /* a bounded device wait ran out */
-  DG_ERR_UNSUPPORTED = 8     /* valid request this build does not implement */
+  DG_ERR_UNSUPPORTED = 8     /* valid request the library does not implement */
 } dg_status;
 
 /* Periodic structured mesh of boxes on [lo, hi] (quads for dim 2, hexes for

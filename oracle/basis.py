@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
 The paper's broken space holds polynomials of degree <= k on each element
-(eq. BSpace).  On quads/hexes this build uses the total-degree space P_p:
+(eq. BSpace).  On quads/hexes the default is the total-degree space P_p:
 products of orthonormal 1-D Legendre polynomials
     phi_a(xi) = prod_k Lt_{a_k}(xi_k),   sum_k a_k <= p,
 on the reference cube [-1, 1]^d, where Lt_n = sqrt((2n+1)/2) P_n.  Modes are
