@@ -63,3 +63,38 @@ def test_batch_cases_seeded():
     b = wl.batch_cases(8)
     assert a == b and len(a) == 8
     assert all(1 <= c["p"] <= 5 and 8 <= c["n"][0] <= 24 for c in a)
+
+
+def test_tri_mesh_seeded_ccw_and_covering():
+    cfg = wl.tri_config((5, 4), 2)
+    a, b = wl.tri_mesh(cfg), wl.tri_mesh(cfg)
+    for k in ("X", "tri", "shift"):
+        assert np.array_equal(a[k], b[k])                       # same seed, same mesh
+    other = wl.tri_mesh(dict(cfg, seed=7))
+    assert not np.array_equal(other["X"], a["X"])
+    L = a["hi"] - a["lo"]
+    V = a["X"][a["tri"]] + a["shift"] * L[None, None, :]
+    area = 0.5 * ((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1])
+                  - (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
+    assert np.all(area > 0.0)                                    # counter-clockwise
+    assert abs(area.sum() - L[0] * L[1]) < 1e-9 * L[0] * L[1]    # the triangles tile the box
+    assert a["tri"].shape == (2 * 5 * 4, 3) and wl.tri_state_shape(cfg) == (40, 4, 6)
+
+
+def test_tri_projection_exact_for_polynomials():
+    """The Dubiner projection reproduces a field of degree <= p at any point."""
+    from scipy.special import eval_jacobi
+    cfg = wl.tri_config((3, 2), 3)
+    f = lambda X: [1.0 + 0.1 * X[..., 0] ** 2 * X[..., 1] - 0.02 * X[..., 1] ** 3 + 0.0 * X[..., 0]] * 4
+    W = wl.tri_project(cfg, f)
+    msh = wl.tri_mesh(cfg)
+    L = msh["hi"] - msh["lo"]
+    V = msh["X"][msh["tri"]] + msh["shift"] * L[None, None, :]
+    r, s = 0.1 - 0.7, -0.35                                      # one reference point inside T
+    a, b = 2.0 * (1.0 + r) / (1.0 - s) - 1.0, s
+    psi = np.array([math.sqrt(2.0) * eval_jacobi(i, 0, 0, a) / math.sqrt(2.0 / (2 * i + 1))
+                    * eval_jacobi(j, 2 * i + 1, 0, b) / math.sqrt(2.0 ** (2 * i + 2) / (2 * j + 2 * i + 2))
+                    * (1.0 - b) ** i for i, j in wl.tri_modes(3)])
+    X = V[:, 0] + (r + 1.0) / 2.0 * (V[:, 1] - V[:, 0]) + (s + 1.0) / 2.0 * (V[:, 2] - V[:, 0])
+    exact = f(X[:, None, :])[0][:, 0]
+    assert np.abs(W[:, 0, :] @ psi - exact).max() < 1e-12
