@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-esdirk", action="store_true")
     ap.add_argument("--no-bilu", action="store_true")
     ap.add_argument("--no-triangles", action="store_true")
+    ap.add_argument("--no-qspace", action="store_true")
     return ap.parse_args()
 
 
@@ -297,6 +298,37 @@ def triangle_steps(torch, B, stream, newton, flush, steps=2):
                            "mixed pMG 4-2-1-0 nu 10/10/30, %d Newton/step" % newton}
         pmg.close()
         mesh.close()
+        return out
+    except Exception as exc:                 # reported in the JSON line, the headline stands
+        return {"error": "%s: %s" % (type(exc).__name__, exc)}
+
+
+def q_space_jvp(torch, B, stream, n=10):
+    """The exact JVP on the tensor-product space Q_4 (TGV 16^3 hexes, 125 modes
+    per variable): the volume term runs by sum factorisation.  Mean device time
+    of n back-to-back FP64 and FP32 JVPs after three untimed ones, with the
+    P_4 JVP of the same mesh beside it (35 modes, direct contractions)."""
+    out = {}
+    try:
+        for space in ("Q", "P"):
+            cfg = wl.make_config("tgv", 3, (16, 16, 16), 4, M=0.1, Re=1600.0, space=space)
+            mesh = B.Mesh.from_workload(wl.mesh_desc(cfg), wl.physics(cfg), stream=stream)
+            W = torch.from_numpy(wl.perturbed_state(cfg)).cuda()
+            v = torch.from_numpy(wl.random_vector(W.shape)).cuda()
+            Kv = torch.empty_like(W)
+            rec = {"dofs": mesh.ndofs}
+            for name, mode in (("fp64_ms", B.JVP_EXACT), ("fp32_ms", B.JVP_EXACT_FP32)):
+                for _ in range(3):
+                    mesh.jvp(W, v, Kv, 100.0, mode=mode, stream=stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(n):
+                    mesh.jvp(W, v, Kv, 100.0, mode=mode, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                rec[name] = e0.elapsed_time(e1) / n
+            out[space] = rec
+            mesh.close()
         return out
     except Exception as exc:                 # reported in the JSON line, the headline stands
         return {"error": "%s: %s" % (type(exc).__name__, exc)}
@@ -556,6 +588,7 @@ def run_gb300(args):
                                                         stream, flush)
         bilu = None if args.no_bilu else coarse_bilu_steps(torch, B, cfg, stream, W0, Wm1, args.newton, flush)
         tris = None if args.no_triangles else triangle_steps(torch, B, stream, args.newton, flush)
+        qsp = None if args.no_qspace else q_space_jvp(torch, B, stream)
         # end to end through the public API with pinned host buffers
         e2e = None
         if not args.no_e2e:
@@ -612,6 +645,7 @@ def run_gb300(args):
         "esdirk3": esd,
         "coarse_bilu": bilu,
         "triangles": tris,
+        "q_space_jvp": qsp,
         "clocks": clk, "gpu_launches": launches, "e2e": e2e,
     }
     if not args.no_batched:
