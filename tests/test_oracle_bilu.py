@@ -218,3 +218,16 @@ def test_bilu_beats_block_jacobi_as_coarse_smoother(kind):
         x = gmres_fixed(K, P, b, np.zeros_like(b), 4)
         res[name] = np.linalg.norm(b - K(x)) / np.linalg.norm(b)
     assert res[kind] < res["bj"], res
+
+
+def test_mdf_reduced_weights_closed_form():
+    """c_ij = ||A_ii^{-1} A_ij||_F: with A_ii = a I and A_ij = b_ij I on nb x nb
+    blocks, c_ij = |b_ij| / a * sqrt(nb)."""
+    nb = 5
+    nbrs = [{1, 2}, {0}, {0}]
+    A = {(0, 0): 2.0 * np.eye(nb), (1, 1): 4.0 * np.eye(nb), (2, 2): 0.5 * np.eye(nb),
+         (0, 1): 3.0 * np.eye(nb), (0, 2): -1.0 * np.eye(nb), (1, 0): 2.0 * np.eye(nb), (2, 0): 0.25 * np.eye(nb)}
+    c = bilu.mdf_weights_c(A, nbrs)
+    for (i, j), b in (((0, 1), 3.0), ((0, 2), -1.0), ((1, 0), 2.0), ((2, 0), 0.25)):
+        a = A[(i, i)][0, 0]
+        assert abs(c[(i, j)] - abs(b) / a * np.sqrt(nb)) < 1e-14
