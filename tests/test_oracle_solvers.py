@@ -191,3 +191,112 @@ def test_pmg_preconditioned_fgmres_step():
     assert st["iters"] <= st2["iters"]
     assert np.linalg.norm(b - K(x)) <= 1.0001e-5 * np.linalg.norm(b)
     assert relmax(x, x2) < 1e-3
+
+
+# ------------------------------------------------------------------ Algorithm 2 written densely
+def _truncation(E, m, nm_f, nm_c):
+    """Dense restriction I_l^{l+1} of the [e][v][i] layout: row (e, v, i) of the
+    coarse vector takes entry (e, v, i) of the fine one, i < nm_c (Sec. 6.1:
+    M_{l+1,l} = [I 0] for an orthonormal hierarchical basis)."""
+    R = np.zeros((E * m * nm_c, E * m * nm_f))
+    for e in range(E):
+        for v in range(m):
+            for i in range(nm_c):
+                R[(e * m + v) * nm_c + i, (e * m + v) * nm_f + i] = 1.0
+    return R
+
+
+def _block_jacobi_dense(A, nb):
+    """Inverse of the element-diagonal part of A (blocks of size nb)."""
+    P = np.zeros_like(A)
+    for s in range(0, A.shape[0], nb):
+        P[s:s + nb, s:s + nb] = np.linalg.inv(A[s:s + nb, s:s + nb])
+    return P
+
+
+def _gmres1(A, P, b, x):
+    """One right-preconditioned GMRES iteration from x in closed form:
+    x + alpha P r with alpha minimising ||r - alpha A P r||."""
+    r = b - A @ x
+    z = P @ r
+    w = A @ z
+    return x + (w @ r) / (w @ w) * z
+
+
+def _dense_vcycle(A, P, R, l, b, x):
+    """Algorithm 2 with one smoothing iteration before and after the coarse
+    correction and an exact solve on the coarsest level; A[l] = R_l K R_l^T is
+    the Galerkin coarse matrix, R[l] the restriction from level l to l + 1."""
+    L = len(A) - 1
+    if l == L:
+        return np.linalg.solve(A[l], b)
+    xb = _gmres1(A[l], P[l], b, x)
+    r = b - A[l] @ xb
+    e = _dense_vcycle(A, P, R, l + 1, R[l] @ r, np.zeros(R[l].shape[0]))
+    xh = xb + R[l].T @ e
+    return _gmres1(A[l], P[l], b, xh)
+
+
+def _levels(mesh, K, p_levels):
+    nms = [wl.n_modes(p, mesh.d) for p in p_levels]
+    R = [_truncation(mesh.E, mesh.m, nms[l], nms[l + 1]) for l in range(len(nms) - 1)]
+    A = [K]
+    for Rl in R:
+        A.append(Rl @ A[-1] @ Rl.T)
+    P = [_block_jacobi_dense(A[l], mesh.m * nms[l]) for l in range(len(A))]
+    return nms, R, A, P
+
+
+def test_vcycle_two_levels_no_smoothing_is_coarse_correction():
+    """MG_V(0, b, 0) with no smoothing and an exact coarsest solve is the
+    coarse-grid correction alone: x = I^T A_1^{-1} I b with A_1 = I K I^T
+    (Algorithm 2); MG_full then adds a second correction of the residual left
+    by the first (Algorithm 1).  A dropped or sign-flipped correction fails."""
+    cfg = wl.make_config("vortex", 2, (3, 2), 1, M=0.5, Re=100.0)
+    mesh, ph, W = _setup(cfg)
+    sigma = 2.0
+    K = _dense_K(mesh, ph, W, sigma)
+    nms, R, A, P = _levels(mesh, K, (1, 0))
+    nc = A[1].shape[0]
+    mg = solvers.pmg_setup(mesh, ph, W, sigma, (1, 0), nu_pre=0, nu_post=0, nu_coarse=nc)
+    b = wl.random_vector(W.shape, 11)
+    bf = b.reshape(-1)
+    x = mg.mg_v(0, b, np.zeros_like(b)).reshape(-1)
+    xd = R[0].T @ np.linalg.solve(A[1], R[0] @ bf)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    # MG_full: x1 = I^T A_1^-1 I b, then one more correction of b - K x1
+    xf = mg.mg_full(b).reshape(-1)
+    x1 = R[0].T @ np.linalg.solve(A[1], R[0] @ bf)
+    xf_d = x1 + R[0].T @ np.linalg.solve(A[1], R[0] @ (bf - K @ x1))
+    assert np.linalg.norm(xf - xf_d) <= 1e-9 * np.linalg.norm(xf_d)
+
+
+def test_vcycle_three_levels_against_dense_algorithm():
+    """Three levels p = 2, 1, 0 with one GMRES(BJ) smoothing step before and
+    after each coarse correction and an exact coarsest solve: the oracle's
+    MG_V and MG_full equal Algorithms 1-2 written with dense Galerkin matrices
+    R K R^T (independent of the inherited BSR blocks), dense block-Jacobi
+    inverses and GMRES(1) in closed form."""
+    cfg = wl.make_config("vortex", 2, (3, 2), 2, M=0.5, Re=100.0)
+    mesh, ph, W = _setup(cfg)
+    sigma = 3.0
+    K = _dense_K(mesh, ph, W, sigma)
+    nms, R, A, P = _levels(mesh, K, (2, 1, 0))
+    mg = solvers.pmg_setup(mesh, ph, W, sigma, (2, 1, 0), nu_pre=1, nu_post=1,
+                           nu_coarse=A[2].shape[0])
+    b = wl.random_vector(W.shape, 12)
+    x0 = 0.1 * wl.random_vector(W.shape, 13)
+    bf = b.reshape(-1)
+    xv = mg.mg_v(0, b, x0).reshape(-1)
+    xv_d = _dense_vcycle(A, P, R, 0, bf, x0.reshape(-1))
+    assert np.linalg.norm(xv - xv_d) <= 1e-9 * np.linalg.norm(xv_d)
+    # Algorithm 1: b_l = I_0^l b; coarsest solve; prolong and V-cycle upwards
+    bl = [bf, R[0] @ bf, R[1] @ (R[0] @ bf)]
+    x = np.linalg.solve(A[2], bl[2])
+    for l in (1, 0):
+        x = _dense_vcycle(A, P, R, l, bl[l], R[l].T @ x)
+    xf = mg.mg_full(b).reshape(-1)
+    assert np.linalg.norm(xf - x) <= 1e-9 * np.linalg.norm(x)
+    # the coarse correction matters here: without it the result moves by O(1)
+    xb = _gmres1(A[0], P[0], bf, x0.reshape(-1))
+    assert np.linalg.norm(_gmres1(A[0], P[0], bf, xb) - xv_d) > 1e-3 * np.linalg.norm(xv_d)
