@@ -136,13 +136,17 @@ dg_status dg_residual(dg_mesh mesh, const double* W, const double* S, double* R,
  * ask for a residual (the paper has no counterpart: this is a library-usage
  * entry point).  Such callers include applications that reserve all device
  * memory at start-up and time-critical loops that must stay out of the CUDA
- * allocator.  Same result and arguments as dg_residual, same kernels; the
- * face-slot scratch is a fixed file-scope device array of 2^20 doubles (8 MiB)
- * that every GPU loading the library holds until the process exits, instead
- * of the mesh handle's workspace.
+ * allocator.  Same arguments as dg_residual and the same result: the same
+ * kernels on P_p meshes; on Q_p meshes the volume term takes the direct
+ * contractions where dg_residual sums it by factorisation, so the two agree
+ * to rounding there.  The face-slot scratch is a fixed file-scope device
+ * array of 2^20 doubles (8 MiB) that every GPU loading the library holds
+ * until the process exits, instead of the mesh handle's workspace.
  * Limits: E * dim * 2 * m * n_m must not exceed 2^20, else DG_ERR_INVALID.
- * The first call on a device looks up the array's address with that device
- * current (make it before any stream capture).  All calls share the array:
+ * dg_mesh_create looks up the array on its device (the library's device code
+ * may be loaded lazily, and loading it is what allocates the array), so a
+ * call here, on a mesh handle that exists, allocates nothing; mesh creation
+ * reports DG_ERR_OOM if the array cannot be loaded.  All calls share the array:
  * calls that may overlap on the GPU race, so order them on one stream.
  * The array keeps the last call's contents; nothing in it needs clearing,
  * since each call writes every slot it reads. */
@@ -179,6 +183,11 @@ dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma,
 #define DG_ORDER_NATURAL 1  /* element index order */
 #define DG_ORDER_COLOUR 2   /* greedy multicolour order (few substitution levels) */
 
+#define DG_STORE_NATIVE 0   /* blocks stored in the handle's precision (FP64, or FP32 in mixed mode) */
+#define DG_STORE_BF16 1     /* mixed mode: the smoothers stream BF16 copies of the inverse diagonal
+                               blocks of every level and of the inherited coarse blocks (rounded to
+                               nearest from the FP32 blocks at setup/refresh), multiplying in FP32 */
+
 /* p-multigrid options (Sec. 6; Table MGSettings).  p_level[0] must equal the
  * mesh degree and the levels must decrease strictly.  Every smoother is GMRES
  * right-preconditioned by element block Jacobi, except the coarsest one with
@@ -186,7 +195,13 @@ dg_status dg_jvp(dg_mesh mesh, const double* W, const double* R_W, double sigma,
  * periodic direction of exactly 3 elements, and a coarsest block of at most
  * 64 rows in FP64 / 90 in FP32); nu_pre/nu_post (0..64) per level (ignored on
  * the coarsest), nu_coarse (1..64) on the coarsest level.  A zero-initialised
- * tail (coarse_precond, coarse_order) selects block Jacobi. */
+ * tail (coarse_precond, coarse_order, block_storage) selects block Jacobi with
+ * blocks in the handle's precision.  block_storage = DG_STORE_BF16 needs
+ * precision DG_PREC_MIXED and blocks of at most 2048 rows (fine) and
+ * (1 + 2 dim) * ceil(nb / 8) <= 256 on coarse levels; else DG_ERR_INVALID.
+ * The FP32 blocks are kept beside the BF16 copies (the inversion and the
+ * block ILU(0) use them); dg_pmg_export_blocks returns the BF16 values the
+ * smoothers use for DG_BLOCKS_DIAG_INV and DG_BLOCKS_NEIGHBOUR. */
 typedef struct {
   int n_levels;
   int p_level[8];
@@ -196,6 +211,7 @@ typedef struct {
   int fgmres_restart;   /* size of the outer FGMRES workspace allocated here (0 => 30, <= 64) */
   int coarse_precond;   /* DG_COARSE_BJ or DG_COARSE_BILU */
   int coarse_order;     /* DG_ORDER_*: element order of the block ILU(0) */
+  int block_storage;    /* DG_STORE_NATIVE or DG_STORE_BF16 */
 } dg_pmg_opts;
 
 /* Assemble the preconditioner at state W and shift sigma (once per time step:
@@ -372,6 +388,36 @@ dg_status dg_bilu_order(int n_elem, int n_faces, const int* nbr, const double* c
  * NULL).  Synchronises `stream` first.  DG_ERR_INVALID if the handle has no
  * block ILU(0). */
 dg_status dg_pmg_bilu_order(dg_pmg pmg, int* order, int* n_levels, void* stream);
+
+/* y = A_l x: the operator level `level` of the handle smooths with (Sec. 6.1):
+ * level 0 the matrix-free Jacobian-vector product sigma M x + dR/dW(W) x at
+ * the handle's state and shift (in mixed precision the FP32 product the
+ * smoother uses, with the state's traces cached at setup/refresh), levels >= 1
+ * the inherited block-sparse operator D_e x_e + sum_s O_{e,s} x_nbr(e,s) on
+ * the leading n_m(p_level[level]) modes of every variable.  x, y: device FP64,
+ * E * m * n_m(p_level[level]) entries, may not alias (widened from FP32 in
+ * mixed mode).  For testing and inspection; uses the handle's staging
+ * buffers, so it must not overlap other calls on the handle.  DG_ERR_INVALID
+ * if the level does not exist. */
+dg_status dg_pmg_operator(dg_pmg pmg, int level, const double* x, double* y, void* stream);
+
+#define DG_KT_FACE_JVP 0      /* face kernel of the fine-level operator (level 0) */
+#define DG_KT_VOLUME_JVP 1    /* volume kernel of the fine-level operator (level 0) */
+#define DG_KT_BLOCK_JACOBI 2  /* block-Jacobi apply of the level */
+#define DG_KT_OPERATOR 3      /* the level's operator (level >= 1: the block-sparse product) */
+#define DG_KT_SMOOTH 4        /* one smoother call of the level (nu_pre iterations; nu_coarse on the coarsest) */
+
+/* Mean device time in ms (*ms, host) of one kernel of the handle's solve path,
+ * launched `reps` (>= 1) times back to back on `stream` between two CUDA
+ * events, for benchmarks and roofline reports: the fine-level operator's face
+ * or volume kernel (the FP32 smoother JVP with the state's cached traces in
+ * mixed mode, the FP64 JVP in an FP64 handle), the block-Jacobi apply, the
+ * operator or one smoother call of `level`.  Inputs are a fixed pattern in the
+ * handle's own level vectors; the results are discarded (the vectors, not the
+ * blocks, are overwritten).  The mesh must be structured.  Synchronises
+ * `stream`.  DG_ERR_INVALID for a bad kernel or level (the face and volume
+ * kernels belong to level 0; a block-Jacobi-only handle has no smoother). */
+dg_status dg_pmg_kernel_time(dg_pmg pmg, int kernel, int level, int reps, float* ms, void* stream);
 
 /* Sizes of the pMG workspace in bytes (blocks, vectors), for memory budgeting. */
 dg_status dg_pmg_bytes(dg_pmg pmg, size_t* block_bytes, size_t* vector_bytes);

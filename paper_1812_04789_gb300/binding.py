@@ -11,7 +11,8 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libdgpmg.so")
 
-DG_OK = 0
+DG_OK, DG_ERR_INVALID, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_NONPHYSICAL = 0, 1, 2, 3, 4
+DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_TIMEOUT, DG_ERR_UNSUPPORTED = 5, 6, 7, 8
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_INVALID", 2: "DG_ERR_OOM", 3: "DG_ERR_CUDA",
                 4: "DG_ERR_NONPHYSICAL", 5: "DG_ERR_NOT_CONVERGED", 6: "DG_ERR_BREAKDOWN",
                 7: "DG_ERR_TIMEOUT", 8: "DG_ERR_UNSUPPORTED"}
@@ -22,11 +23,14 @@ SPACE_P, SPACE_Q = 0, 1
 BLOCKS_DIAG_INV, BLOCKS_NEIGHBOUR, BLOCKS_DIAG = 0, 1, 2
 COARSE_BJ, COARSE_BILU = 0, 1
 ORDER_MDF, ORDER_NATURAL, ORDER_COLOUR = 0, 1, 2
+STORE_NATIVE, STORE_BF16 = 0, 1
+KT_FACE_JVP, KT_VOLUME_JVP, KT_BLOCK_JACOBI, KT_OPERATOR, KT_SMOOTH = 0, 1, 2, 3, 4
 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_mesh_info", "dg_residual", "dg_jvp",
             "dg_pmg_setup", "dg_pmg_apply", "dg_pmg_destroy", "dg_fgmres_step", "dg_status_sync",
             "dg_pmg_bytes", "dg_pmg_export_blocks", "dg_bdf2_rhs", "dg_axpy", "dg_launch_count", "dg_pmg_refresh", "dg_residual_noalloc",
-            "dg_esdirk3_rhs", "dg_esdirk3_step", "dg_bilu_order", "dg_pmg_bilu_order", "dg_mesh_create_tri"]
+            "dg_esdirk3_rhs", "dg_esdirk3_step", "dg_bilu_order", "dg_pmg_bilu_order", "dg_mesh_create_tri",
+            "dg_pmg_operator", "dg_pmg_kernel_time"]
 
 
 class DGError(RuntimeError):
@@ -57,7 +61,7 @@ class PmgOpts(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_int), ("p_level", ctypes.c_int * 8), ("nu_pre", ctypes.c_int * 8),
                 ("nu_post", ctypes.c_int * 8), ("nu_coarse", ctypes.c_int), ("cycle", ctypes.c_int),
                 ("precision", ctypes.c_int), ("fgmres_restart", ctypes.c_int), ("coarse_precond", ctypes.c_int),
-                ("coarse_order", ctypes.c_int)]
+                ("coarse_order", ctypes.c_int), ("block_storage", ctypes.c_int)]
 
 
 class KrylovOpts(ctypes.Structure):
@@ -112,6 +116,8 @@ def load(path=None):
                           ctypes.POINTER(ctypes.c_int)],
         "dg_pmg_bilu_order": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), P],
         "dg_mesh_create_tri": [ctypes.POINTER(TriDesc), ctypes.POINTER(PhysicsDesc), P, ctypes.POINTER(P)],
+        "dg_pmg_operator": [P, ctypes.c_int, P, P, P],
+        "dg_pmg_kernel_time": [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_float), P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -273,7 +279,7 @@ def launch_count():
 
 
 def pmg_opts(p_levels, nu_pre=10, nu_post=10, nu_coarse=30, cycle=CYCLE_FMG, precision=PREC_FP64,
-             fgmres_restart=30, coarse=COARSE_BJ, order=ORDER_MDF):
+             fgmres_restart=30, coarse=COARSE_BJ, order=ORDER_MDF, storage=0):
     o = PmgOpts()
     o.n_levels = len(p_levels)
     for l, p in enumerate(p_levels):
@@ -286,6 +292,7 @@ def pmg_opts(p_levels, nu_pre=10, nu_post=10, nu_coarse=30, cycle=CYCLE_FMG, pre
     o.fgmres_restart = int(fgmres_restart)
     o.coarse_precond = int(coarse)
     o.coarse_order = int(order)
+    o.block_storage = int(storage)
     return o
 
 
@@ -350,6 +357,17 @@ class PMG:
         a, b = ctypes.c_size_t(), ctypes.c_size_t()
         _check("dg_pmg_bytes", load().dg_pmg_bytes(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def operator(self, level, x, y, stream=None):
+        """y = A_level x (dg_pmg_operator): the operator the level's smoother uses."""
+        _check("dg_pmg_operator", load().dg_pmg_operator(self.h, int(level), _ptr(x), _ptr(y), _stream(stream)))
+
+    def kernel_time(self, kernel, level=0, reps=10, stream=None):
+        """Mean device ms of one kernel of the solve path (dg_pmg_kernel_time)."""
+        ms = ctypes.c_float()
+        _check("dg_pmg_kernel_time", load().dg_pmg_kernel_time(self.h, int(kernel), int(level), int(reps),
+                                                               ctypes.byref(ms), _stream(stream)))
+        return ms.value
 
     def export_blocks(self, level, which, out, stream=None):
         nbytes = out.numel() * out.element_size()

@@ -92,7 +92,19 @@ template <class T>
 cudaError_t MG<T>::op(int l, const T* x, T* y, cudaStream_t st) {
   if (l == 0) return launch_residual<T>(*mesh, W, x, nullptr, sigma, true, y, st, Pv, Pf);
   Level<T>& L = lv[l];
+  if (L.Dop16)   // BF16 storage (FP32 handles only)
+    return launch_bsr_bf16(L.Dop16, L.O16, mesh->face_nbr(), mesh->nfaces(), reinterpret_cast<const float*>(x),
+                           reinterpret_cast<float*>(y), L.nb, mesh->E, st);
   return launch_bsr<T>(L.Dop, L.O, L.cs, L.co_t, mesh->face_nbr(), mesh->nfaces(), x, y, L.nb, mesh->E, st);
+}
+
+// z = D_l^{-1} r with the level's stored inverses (block Jacobi, Sec. 6.3).
+template <class T>
+static cudaError_t bj_apply(const Level<T>& L, const T* r, T* z, int E, cudaStream_t st) {
+  if (L.Dinv16)
+    return launch_block_apply_bf16(L.Dinv16, reinterpret_cast<const float*>(r), reinterpret_cast<float*>(z), L.nb,
+                                   E, st);
+  return launch_block_apply<T>(L.Dinv, L.bs, L.inv_t, r, z, L.nb, E, st);
 }
 
 // SMOOTH / SOLVE: nu iterations of GMRES right-preconditioned by block Jacobi
@@ -102,6 +114,16 @@ template <class T>
 cudaError_t MG<T>::smooth(int l, const T* b, T* x, int nu, cudaStream_t st) {
   Level<T>& L = lv[l];
   Krylov<T>& K = L.kr;
+  if constexpr (std::is_same<T, float>::value) {
+    // inherited FP32/BF16 coarse levels: the whole call in one persistent launch
+    const bool ilu = bilu && l == (int)lv.size() - 1;
+    if (l >= 1 && L.coop.ok && !ilu && (L.Dinv16 || (L.inv_t && L.co_t))) {
+      if (nu == 0) return cudaSuccess;
+      return launch_coop_smoother(L.coop, L.Dinv, L.Dop, L.O, L.Dinv16, L.Dop16, L.O16, mesh->face_nbr(),
+                                  mesh->nfaces(), b, x, nu, K, L.cpart, L.cbar, mesh->status, coop_extra, L.nb,
+                                  mesh->E, st);
+    }
+  }
   CKE(op(l, x, L.r, st));
   CKE(launch_axpby<T>(L.N, 1.0, b, -1.0, L.r, st));           // r = b - A x
   CKE(K.start(L.r, st));
@@ -110,7 +132,7 @@ cudaError_t MG<T>::smooth(int l, const T* b, T* x, int nu, cudaStream_t st) {
     if (ilu)
       CKE(launch_bilu_apply<T>(*this, K.Vj(j), K.Zj(j), st));
     else
-      CKE(launch_block_apply<T>(L.Dinv, L.bs, L.inv_t, K.Vj(j), K.Zj(j), L.nb, mesh->E, st));
+      CKE(bj_apply<T>(L, K.Vj(j), K.Zj(j), mesh->E, st));
     CKE(op(l, K.Zj(j), K.w, st));
     CKE(K.arnoldi(j, st));
   }
@@ -140,7 +162,7 @@ cudaError_t MG<T>::apply(const T* r, T* z, cudaStream_t st) {
   const int Lc = (int)lv.size() - 1;
   const long nev = (long)mesh->E * mesh->m;
   if (cycle == DG_CYCLE_BJ)
-    return launch_block_apply<T>(lv[0].Dinv, lv[0].bs, lv[0].inv_t, r, z, lv[0].nb, mesh->E, st);
+    return bj_apply<T>(lv[0], r, z, mesh->E, st);
   if (cycle == DG_CYCLE_V) {
     CKE(cudaMemcpyAsync(lv[0].b, r, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st));
     CKE(cudaMemsetAsync(lv[0].x, 0, sizeof(T) * lv[0].N, st));
@@ -178,6 +200,8 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
   const dg_pmg_opts& o = h->opts;
   mg.mesh = &M;
   mg.nu_coarse = o.nu_coarse;
+  const char* extra = getenv("DG_TEST_COOP_BARRIER_EXTRA");   // test hook: a barrier that is never met
+  mg.coop_extra = extra ? std::max(0, atoi(extra)) : 0;
   mg.cycle = o.cycle;
   const int nl = o.cycle == DG_CYCLE_BJ ? 1 : o.n_levels;
   mg.lv.resize(nl);
@@ -213,11 +237,35 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
       CK(cudaMemset(L.Dop, 0, sizeof(T) * (size_t)M.E * L.cs));   // padding rows stay zero
       CK(cudaMemset(L.O, 0, sizeof(T) * (size_t)M.E * M.nfaces() * L.cs));
     }
+    if (o.block_storage == DG_STORE_BF16) {   // mixed precision only (check_opts)
+      const size_t b16 = (size_t)L.nb * ld_bf16(L.nb) * sizeof(unsigned short);
+      CK(dalloc(mg.allocs, (void**)&L.Dinv16, b16 * M.E, &h->block_bytes));
+      if (l >= 1) {
+        CK(dalloc(mg.allocs, (void**)&L.Dop16, b16 * M.E, &h->block_bytes));
+        CK(dalloc(mg.allocs, (void**)&L.O16, b16 * M.E * M.nfaces(), &h->block_bytes));
+      }
+    }
     for (T** v : {&L.x, &L.b, &L.r, &L.t}) CK(dalloc(mg.allocs, (void**)v, sizeof(T) * L.N, &h->vector_bytes));
     int nmax = (l == nl - 1) ? std::max(1, o.nu_coarse) : std::max(std::max(L.nu_pre, L.nu_post), 1);
     if (o.cycle != DG_CYCLE_BJ) {
       CK(L.kr.alloc(L.N, nmax));
       h->vector_bytes += L.kr.bytes();
+    }
+    // persistent smoother of an inherited FP32 level (column-major or BF16
+    // blocks, face-neighbour graph of the structured mesh); DG_PMG_NO_COOP=1
+    // keeps the launch-per-operation smoother
+    const char* nco = getenv("DG_PMG_NO_COOP");
+    const bool bf16 = o.block_storage == DG_STORE_BF16;
+    if (std::is_same<T, float>::value && l >= 1 && o.cycle != DG_CYCLE_BJ && M.kind == DG_MESH_STRUCTURED &&
+        (L.co_t || bf16) && !(nco && nco[0] == '1') &&
+        !(o.coarse_precond == DG_COARSE_BILU && l == nl - 1)) {
+      CK(plan_coop_smoother(bf16 ? 1 : 0, L.nb, M.nfaces(), M.E, nmax, &L.coop));
+      if (L.coop.ok) {
+        L.coop.nu_max = nmax;
+        CK(dalloc(mg.allocs, (void**)&L.cpart, sizeof(double) * (size_t)L.coop.grid * (2 * (nmax + 1) + 1),
+                  &h->vector_bytes));
+        CK(dalloc(mg.allocs, (void**)&L.cbar, sizeof(unsigned) * 4, &h->vector_bytes));
+      }
     }
   }
   // primal traces of the fine JVP's linearisation point (FP32 smoother JVPs);
@@ -298,6 +346,16 @@ static dg_status compute_mg(dg_pmg h, MG<T>& mg, const double* W64, cudaStream_t
   }
   for (int l = 0; l < nl; ++l)
     CK(launch_block_inverse<T>(mg.lv[l].Dinv, mg.lv[l].nb, mg.lv[l].bs, M.E, M.status, &mg.lv[l].inv_t, st));
+  for (int l = 0; l < nl; ++l) {   // BF16 copies the smoothers stream (round to nearest)
+    Level<T>& L = mg.lv[l];
+    if (!L.Dinv16) continue;
+    CK(launch_to_bf16(reinterpret_cast<const float*>(L.Dinv), L.bs, L.inv_t, L.Dinv16, L.nb, M.E, st));
+    if (l >= 1) {
+      CK(launch_to_bf16(reinterpret_cast<const float*>(L.Dop), L.cs, L.co_t, L.Dop16, L.nb, M.E, st));
+      CK(launch_to_bf16(reinterpret_cast<const float*>(L.O), L.cs, L.co_t, L.O16, L.nb, (long)M.E * M.nfaces(),
+                        st));
+    }
+  }
   if (mg.bilu) CK(bilu_refresh<T>(mg, st));
   return DG_OK;
 }
@@ -391,6 +449,23 @@ static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
   if (o->precision != DG_PREC_FP64 && o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
   if (o->fgmres_restart < 0 || o->fgmres_restart > 64) return DG_ERR_INVALID;
   if (o->coarse_precond != DG_COARSE_BJ && o->coarse_precond != DG_COARSE_BILU) return DG_ERR_INVALID;
+  if (o->block_storage != DG_STORE_NATIVE && o->block_storage != DG_STORE_BF16) return DG_ERR_INVALID;
+  if (o->block_storage == DG_STORE_BF16) {
+    // FP32 handles only; the BSR kernel runs a thread per block and 8 rows of every element
+    if (o->precision != DG_PREC_MIXED) return DG_ERR_INVALID;
+    const int nl = o->cycle == DG_CYCLE_BJ ? 1 : o->n_levels;
+    for (int l = 0; l < nl && l < 8; ++l) {
+      const int p = o->cycle == DG_CYCLE_BJ ? mesh->m.p : o->p_level[l];
+      long c = 1;
+      if (mesh->m.desc.space == DG_SPACE_Q)
+        for (int i = 1; i <= mesh->m.d; ++i) c *= p + 1;
+      else
+        for (int i = 1; i <= mesh->m.d; ++i) c = c * (p + i) / i;
+      const int nb = mesh->m.m * (int)c;
+      if (ld_bf16(nb) / 8 > 256 || (l >= 1 && (1 + mesh->m.nfaces()) * (ld_bf16(nb) / 8) > 256))
+        return DG_ERR_INVALID;
+    }
+  }
   if (o->coarse_precond == DG_COARSE_BILU) {
     // neighbour blocks exist from level 1; the pivot-block form of ILU(0)
     // needs a face graph without triangles (no periodic direction of 3)
@@ -525,6 +600,90 @@ extern "C" dg_status dg_pmg_apply(dg_pmg h, const double* r, double* z, void* st
   return pmg_apply_impl(h, r, z, (cudaStream_t)stream);
 }
 
+extern "C" dg_status dg_pmg_operator(dg_pmg h, int level, const double* x, double* y, void* stream) {
+  if (!h || !x || !y || x == y) return DG_ERR_INVALID;
+  const bool f64 = h->precision == DG_PREC_FP64;
+  const int nl = (int)(f64 ? h->mg64.lv.size() : h->mg32.lv.size());
+  if (level < 0 || level >= nl) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (f64) {
+    CK(h->mg64.op(level, x, y, st));
+    return DG_OK;
+  }
+  const long N = h->mg32.lv[level].N;   // <= the fine level's size of the staging buffers
+  CK(launch_convert<double, float>(N, x, h->r32, st));
+  CK(h->mg32.op(level, h->r32, h->z32, st));
+  CK(launch_convert<float, double>(N, h->z32, y, st));
+  return DG_OK;
+}
+
+namespace dgk {
+// deterministic non-zero input for kernel timing: x[i] in [-1e-3, 1e-3)
+template <class T>
+__global__ void fill_pattern_kernel(T* x, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    x[i] = (T)(1e-3 * ((double)((i * 7919) % 1000) - 500.0) / 500.0);
+}
+
+template <class T>
+static dg_status time_kernel(MG<T>& mg, const Mesh& M, int kernel, int level, int reps, float* ms,
+                             cudaStream_t st) {
+  Level<T>& L = mg.lv[level];
+  const int grid = (int)std::min<long>((L.N + 255) / 256, 4096);
+  note_launch();
+  fill_pattern_kernel<T><<<grid, 256, 0, st>>>(L.r, L.N);
+  note_launch();
+  fill_pattern_kernel<T><<<grid, 256, 0, st>>>(L.b, L.N);
+  CK(cudaMemsetAsync(L.x, 0, sizeof(T) * L.N, st));
+  const int nu = level == (int)mg.lv.size() - 1 ? mg.nu_coarse : std::max(1, L.nu_pre);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    switch (kernel) {
+      case DG_KT_FACE_JVP:
+        e = launch_residual<T>(M, mg.W, L.r, nullptr, mg.sigma, true, L.t, st, mg.Pv, mg.Pf, 1);
+        break;
+      case DG_KT_VOLUME_JVP:
+        e = launch_residual<T>(M, mg.W, L.r, nullptr, mg.sigma, true, L.t, st, mg.Pv, mg.Pf, 2);
+        break;
+      case DG_KT_BLOCK_JACOBI:
+        e = bj_apply<T>(L, L.r, L.t, M.E, st);
+        break;
+      case DG_KT_OPERATOR:
+        e = mg.op(level, L.r, L.t, st);
+        break;
+      default:
+        e = mg.smooth(level, L.b, L.x, nu, st);
+        break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(e);
+  *ms = t / (float)reps;
+  return DG_OK;
+}
+}  // namespace dgk
+
+extern "C" dg_status dg_pmg_kernel_time(dg_pmg h, int kernel, int level, int reps, float* ms, void* stream) {
+  if (!h || !ms || reps < 1 || kernel < DG_KT_FACE_JVP || kernel > DG_KT_SMOOTH) return DG_ERR_INVALID;
+  const Mesh& M = h->mesh->m;
+  const bool f64 = h->precision == DG_PREC_FP64;
+  const int nl = (int)(f64 ? h->mg64.lv.size() : h->mg32.lv.size());
+  if (level < 0 || level >= nl || M.kind != DG_MESH_STRUCTURED) return DG_ERR_INVALID;
+  if ((kernel == DG_KT_FACE_JVP || kernel == DG_KT_VOLUME_JVP) && level != 0) return DG_ERR_INVALID;
+  if (kernel == DG_KT_SMOOTH && (nl == 1 && h->opts.cycle == DG_CYCLE_BJ)) return DG_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  return f64 ? time_kernel<double>(h->mg64, M, kernel, level, reps, ms, st)
+             : time_kernel<float>(h->mg32, M, kernel, level, reps, ms, st);
+}
+
 extern "C" dg_status dg_pmg_bilu_order(dg_pmg h, int* order, int* n_levels, void* stream) {
   if (!h || !n_levels) return DG_ERR_INVALID;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DG_ERR_CUDA;
@@ -553,10 +712,16 @@ static dg_status export_level(const MG<T>& mg, const Mesh& M, T* W, double sigma
   const size_t nblk = which == DG_BLOCKS_NEIGHBOUR ? (size_t)M.E * M.nfaces() : (size_t)M.E;
   if (out_bytes < nblk * nb * nb * sizeof(T)) return DG_ERR_INVALID;
   if (which == DG_BLOCKS_DIAG_INV) {
-    CK(launch_unpack_inverse<T>(L.Dinv, L.bs, L.inv_t, out, nb, (long)nblk, st));
+    if (L.Dinv16)
+      CK(launch_unpack_bf16(L.Dinv16, reinterpret_cast<float*>(out), nb, (long)nblk, st));
+    else
+      CK(launch_unpack_inverse<T>(L.Dinv, L.bs, L.inv_t, out, nb, (long)nblk, st));
   } else if (which == DG_BLOCKS_NEIGHBOUR) {
     if (level < 1) return DG_ERR_INVALID;
-    CK(launch_unpack_inverse<T>(L.O, L.cs, L.co_t, out, nb, (long)nblk, st));
+    if (L.O16)
+      CK(launch_unpack_bf16(L.O16, reinterpret_cast<float*>(out), nb, (long)nblk, st));
+    else
+      CK(launch_unpack_inverse<T>(L.O, L.cs, L.co_t, out, nb, (long)nblk, st));
   } else if (which == DG_BLOCKS_DIAG) {
     if (level == 0 && M.kind == DG_MESH_TRI)   // the fine-level probe again, at the stored state and shift
       CK(launch_probe_blocks_tri<T>(M, W, (T)sigma, out, (size_t)nb * nb, nullptr, 0, mg.lv[0].r, mg.lv[0].t, st));

@@ -22,6 +22,8 @@
 #include <cstdlib>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "dg_internal.h"
 #include "dg_probe.cuh"
 
@@ -665,5 +667,165 @@ template cudaError_t launch_bsr<double>(const double*, const double*, size_t, in
                                         double*, int, int, cudaStream_t);
 template cudaError_t launch_bsr<float>(const float*, const float*, size_t, int, const int*, int, const float*,
                                        float*, int, int, cudaStream_t);
+
+
+// ---------------------------------------------------------------- BF16 block storage
+// Blocks kept in BF16 for the mixed-precision smoothers (the workload's BF16
+// preconditioner storage): column-major with leading dimension ld16 = nb
+// rounded up to 8 (16 bytes), padding rows zero; products and sums in FP32.
+// A thread owns 8 rows of one block and streams its columns with one 16-byte
+// load each (8 BF16 values, widened by a shift), exactly like the FP32
+// column-major kernels with twice the rows per load.
+__global__ void to_bf16_kernel(const float* __restrict__ src, size_t sstride, int src_t, int ld_src,
+                               unsigned short* __restrict__ dst, size_t dstride, int ld16, int nb, long nblk) {
+  const long tot = nblk * (long)nb * ld16;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / ((long)nb * ld16);
+    const int q = (int)(t - b * (long)nb * ld16), c = q / ld16, r = q - c * ld16;
+    float v = 0.f;
+    if (r < nb) v = src[(size_t)b * sstride + (src_t ? (size_t)c * ld_src + r : (size_t)r * nb + c)];
+    dst[(size_t)b * dstride + (size_t)c * ld16 + r] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  }
+}
+
+cudaError_t launch_to_bf16(const float* src, size_t sstride, int src_t, unsigned short* dst, int nb, long nblk,
+                           cudaStream_t st) {
+  const long tot = nblk * (long)nb * ld_bf16(nb);
+  if (tot <= 0) return cudaSuccess;
+  note_launch();
+  to_bf16_kernel<<<(int)std::min<long>((tot + 255) / 256, 65535L * 8), 256, 0, st>>>(
+      src, sstride, src_t, inv_ld<float>(nb), dst, (size_t)nb * ld_bf16(nb), ld_bf16(nb), nb, nblk);
+  return cudaGetLastError();
+}
+
+__global__ void unpack_bf16_kernel(const unsigned short* __restrict__ A, float* __restrict__ out, int nb, int ld16,
+                                   long nblk) {
+  const long tot = nblk * nb * nb;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot; t += (long)gridDim.x * blockDim.x) {
+    const long b = t / ((long)nb * nb);
+    const int rc = (int)(t - b * nb * nb), r = rc / nb, c = rc - r * nb;
+    out[t] = __uint_as_float((unsigned)A[(size_t)b * nb * ld16 + (size_t)c * ld16 + r] << 16);
+  }
+}
+
+cudaError_t launch_unpack_bf16(const unsigned short* A, float* out, int nb, long nblk, cudaStream_t st) {
+  const long tot = nblk * (long)nb * nb;
+  if (tot <= 0) return cudaSuccess;
+  note_launch();
+  unpack_bf16_kernel<<<(int)std::min<long>((tot + 255) / 256, 65535L * 8), 256, 0, st>>>(A, out, nb, ld_bf16(nb),
+                                                                                      nblk);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) bj_bf16_kernel(const unsigned short* __restrict__ A,
+                                                      const float* __restrict__ x, float* __restrict__ y, int nb,
+                                                      int ld16, int E, int epc, int tpe) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* xs = reinterpret_cast<float*>(smem_raw);   // [epc][nb]
+  const int sub = threadIdx.x / tpe, tt = threadIdx.x - sub * tpe;
+  const size_t bstride = (size_t)nb * ld16;
+  for (long e0 = (long)blockIdx.x * epc; e0 < E; e0 += (long)gridDim.x * epc) {
+    const int nl = (int)min((long)epc, E - e0);
+    for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) xs[t] = x[(size_t)e0 * nb + t];
+    __syncthreads();
+    if (sub < nl) {
+      const unsigned short* base = A + (size_t)(e0 + sub) * bstride + 8 * tt;
+      const float* xe = xs + (size_t)sub * nb;
+      float acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < nb; ++c) {
+        float a[8];
+        ld_bf16x8(base + (size_t)c * ld16, a);
+        const float xv = xe[c];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += a[j] * xv;
+      }
+      float* yo = y + (size_t)(e0 + sub) * nb + 8 * tt;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (8 * tt + j < nb) yo[j] = acc[j];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_block_apply_bf16(const unsigned short* A, const float* r, float* z, int nb, int E,
+                                    cudaStream_t st) {
+  const int ld16 = ld_bf16(nb), tpe = ld16 / 8;
+  if (tpe > 256) return cudaErrorInvalidValue;
+  const int epc = std::max(1, 256 / tpe);
+  const int threads = (epc * tpe + 31) / 32 * 32;
+  const int grid = std::min((E + epc - 1) / epc, 8 * num_sms());
+  note_launch();
+  bj_bf16_kernel<<<grid, threads, (size_t)epc * nb * sizeof(float), st>>>(A, r, z, nb, ld16, E, epc, tpe);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) bsr_bf16_kernel(const unsigned short* __restrict__ Dm,
+                                                       const unsigned short* __restrict__ O,
+                                                       const int* __restrict__ nbr, int nf,
+                                                       const float* __restrict__ x, float* __restrict__ y, int nb,
+                                                       int ld16, int E, int epc, int tpe) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nsrc = 1 + nf, tpb = nsrc * tpe;
+  const size_t bstride = (size_t)nb * ld16;
+  float* xs = reinterpret_cast<float*>(smem_raw);   // [epc][nsrc][nb]
+  float* part = xs + (size_t)epc * nsrc * nb;       // [epc][nsrc][ld16]
+  const int sub = threadIdx.x / tpb, r = threadIdx.x - sub * tpb, b = r / tpe, tt = r - b * tpe;
+  for (long e0 = (long)blockIdx.x * epc; e0 < E; e0 += (long)gridDim.x * epc) {
+    const int nl = (int)min((long)epc, E - e0);
+    for (int t = threadIdx.x; t < nl * nsrc * nb; t += blockDim.x) {
+      const int el = t / (nsrc * nb), q = t - el * nsrc * nb, who = q / nb, j = q - who * nb;
+      const long e = e0 + el;
+      const long src = who == 0 ? e : nbr[(size_t)e * nf + who - 1];
+      xs[t] = x[(size_t)src * nb + j];
+    }
+    __syncthreads();
+    if (sub < nl) {
+      const long e = e0 + sub;
+      const unsigned short* base = (b == 0 ? Dm + (size_t)e * bstride : O + ((size_t)e * nf + b - 1) * bstride) +
+                                   8 * tt;
+      const float* xb = xs + ((size_t)sub * nsrc + b) * nb;
+      float acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < nb; ++c) {
+        float a[8];
+        ld_bf16x8(base + (size_t)c * ld16, a);
+        const float xv = xb[c];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += a[j] * xv;
+      }
+      float* pr = part + ((size_t)sub * nsrc + b) * ld16 + 8 * tt;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) pr[j] = acc[j];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) {
+      const int el = t / nb, row = t - el * nb;
+      const float* pe = part + (size_t)el * nsrc * ld16 + row;
+      float sum = 0.f;
+      for (int bb = 0; bb < nsrc; ++bb) sum += pe[(size_t)bb * ld16];
+      y[(size_t)(e0 + el) * nb + row] = sum;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_bsr_bf16(const unsigned short* D, const unsigned short* O, const int* nbr, int nf,
+                            const float* x, float* y, int nb, int E, cudaStream_t st) {
+  const int ld16 = ld_bf16(nb), tpe = ld16 / 8, tpb = (1 + nf) * tpe;
+  if (tpb > 256) return cudaErrorInvalidValue;   // the level cannot use BF16 blocks (checked at setup)
+  const int epc = std::max(1, 256 / tpb);
+  const int threads = (epc * tpb + 31) / 32 * 32;
+  const int grid = std::min((E + epc - 1) / epc, 16 * num_sms());
+  const size_t smem = (size_t)epc * (1 + nf) * (nb + ld16) * sizeof(float);
+  note_launch();
+  bsr_bf16_kernel<<<grid, threads, smem, st>>>(D, O, nbr, nf, x, y, nb, ld16, E, epc, tpe);
+  return cudaGetLastError();
+}
 
 }  // namespace dgk

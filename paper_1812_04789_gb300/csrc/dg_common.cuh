@@ -12,6 +12,23 @@
 
 namespace dgk {
 
+// 8 consecutive BF16 values (16 bytes, read-only, not kept in L1) widened to
+// FP32: a BF16 value is the upper half of the FP32 with the same bits.
+__device__ __forceinline__ void ld_bf16x8(const unsigned short* p, float* v) {
+  unsigned a, b, c, d;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "l"(p));
+  v[0] = __uint_as_float(a << 16);
+  v[1] = __uint_as_float(a & 0xffff0000u);
+  v[2] = __uint_as_float(b << 16);
+  v[3] = __uint_as_float(b & 0xffff0000u);
+  v[4] = __uint_as_float(c << 16);
+  v[5] = __uint_as_float(c & 0xffff0000u);
+  v[6] = __uint_as_float(d << 16);
+  v[7] = __uint_as_float(d & 0xffff0000u);
+}
+
 // ----------------------------------------------------------------- duals
 template <class T>
 struct Dual {

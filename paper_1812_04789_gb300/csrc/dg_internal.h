@@ -104,10 +104,13 @@ struct Mesh {
 // Residual (jvp = false) or exact JVP (jvp = true) in precision T:
 // out = [R(W) - S] or [sigma |J| V + dR/dW(W) V].
 // For a JVP, Pv / Pf (optional, FP32 only) hold the primal traces of W from
-// launch_primal_cache: the kernels then interpolate only V.
+// launch_primal_cache: the kernels then interpolate only V.  parts (structured
+// meshes): 1 = the face kernel only, 2 = the volume kernel only (on the face
+// slots as they are), 3 = both (the operation); parts other than 3 serve
+// kernel timing.
 template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp,
-                            T* out, cudaStream_t st, const T* Pv = nullptr, const T* Pf = nullptr);
+                            T* out, cudaStream_t st, const T* Pv = nullptr, const T* Pf = nullptr, int parts = 3);
 
 // Blocks of a triangle mesh by coloured JVP probing (csrc/dg_tri.cu): D (row-
 // major, dstride apart) = dR_e/dW_e + sigma |J_e| I; O (if given, row-major
@@ -120,6 +123,10 @@ template <class T>
 cudaError_t launch_residual_tri(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
                                 cudaStream_t st);
 void free_mesh(Mesh& M);
+// Look up the allocation-free residual's scratch array on the current device
+// (csrc/dg_noalloc.cu); dg_mesh_create calls it so that the array exists
+// before dg_residual_noalloc is first called.
+dg_status noalloc_prepare();
 
 // Volume part (+ face slots, + sigma |J| V or - S) by sum factorisation for the
 // tensor-product space; cudaErrorNotSupported when the mesh is not Q_p or the
@@ -201,6 +208,20 @@ template <class T>
 cudaError_t launch_unpack_inverse(const T* A, size_t bstride, int transposed, T* out, int nb, long nblk,
                                   cudaStream_t st);
 
+// BF16 block storage (mixed precision): column-major, leading dimension
+// ld_bf16(nb) = nb rounded up to 8 (16 bytes), nb * ld_bf16(nb) entries per
+// block, padding rows zero.  launch_to_bf16 rounds FP32 blocks (layout as in
+// launch_block_apply: column-major with inv_ld<float>(nb) when src_t, else
+// row-major) to nearest; the apply and BSR kernels multiply in FP32.
+constexpr int ld_bf16(int nb) { return (nb + 7) / 8 * 8; }
+cudaError_t launch_to_bf16(const float* src, size_t sstride, int src_t, unsigned short* dst, int nb, long nblk,
+                           cudaStream_t st);
+cudaError_t launch_unpack_bf16(const unsigned short* A, float* out, int nb, long nblk, cudaStream_t st);
+cudaError_t launch_block_apply_bf16(const unsigned short* A, const float* r, float* z, int nb, int E,
+                                    cudaStream_t st);
+cudaError_t launch_bsr_bf16(const unsigned short* D, const unsigned short* O, const int* nbr, int nf,
+                            const float* x, float* y, int nb, int E, cudaStream_t st);
+
 // y = D x + sum_s O_s x_nbr(s); blocks bstride apart (D: [E], O: [E][2d]),
 // column-major with leading dimension inv_ld(nb) when transposed.
 template <class T>
@@ -249,6 +270,27 @@ struct Krylov {
 };
 
 // ----------------------------------------------------------------- pMG
+// Launch plan of the persistent coarse-level smoother (csrc/dg_smoother.cu):
+// grid CTAs (all co-resident, cooperative launch), chunk elements per CTA,
+// epc elements per pass of the block-sparse product, tpe threads per block,
+// dynamic shared memory for up to nu_max iterations.  ok = 0: not available.
+struct CoopPlan {
+  int ok = 0, grid = 0, chunk = 0, epc = 0, tpe = 0, nu_max = 0;
+  size_t smem = 0;
+};
+cudaError_t plan_coop_smoother(int bf16, int nb, int nf, int E, int nu, CoopPlan* plan);
+// One SMOOTH call (nu GMRES(BJ) iterations from x on A x = b, Algorithm 2) in
+// one cooperative launch: FP32 vectors, blocks column-major in FP32 (inv_ld)
+// or, when Dinv16 is given, BF16 (ld_bf16).  part: grid * (2 (nu_max + 1) + 1)
+// doubles; bar: one counter (zeroed by the call, on the stream); a bounded
+// grid barrier that runs out sets ST_TIMEOUT in *status.  expect_extra > 0
+// makes every barrier wait for CTAs that do not exist (the wait then runs out).
+cudaError_t launch_coop_smoother(const CoopPlan& pl, const float* Dinv, const float* Dop, const float* O,
+                                 const unsigned short* Dinv16, const unsigned short* Dop16, const unsigned short* O16,
+                                 const int* nbr, int nf, const float* b, float* x, int nu, Krylov<float>& K,
+                                 double* part, unsigned* bar, int* status, int expect_extra, int nb, int E,
+                                 cudaStream_t st);
+
 template <class T>
 struct Level {
   int p = 0, nm = 0, nb = 0;
@@ -263,6 +305,14 @@ struct Level {
   T *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
   int nu_pre = 0, nu_post = 0;
   Krylov<T> kr;
+  // BF16 copies the smoother streams instead (mixed precision, DG_STORE_BF16):
+  // inverse diagonal blocks, inherited diagonal and neighbour blocks (l >= 1)
+  unsigned short* Dinv16 = nullptr;
+  unsigned short* Dop16 = nullptr;
+  unsigned short* O16 = nullptr;
+  CoopPlan coop;             // persistent smoother (FP32 coarse levels), when available
+  double* cpart = nullptr;   //   its reduction partials
+  unsigned* cbar = nullptr;  //   and barrier counter
 };
 
 template <class T>
@@ -290,6 +340,7 @@ struct MG {
   std::vector<int> h_nbr, h_order, h_level, h_ptr, h_el, h_pos;
   std::vector<double> h_c;
   int h_nlev = 0, h_nlev_buf = 0;
+  int coop_extra = 0;         // test hook: extra barrier arrivals the persistent smoother waits for
   cudaError_t op(int l, const T* x, T* y, cudaStream_t st);
   cudaError_t smooth(int l, const T* b, T* x, int nu, cudaStream_t st);
   cudaError_t mg_v(int l, cudaStream_t st);           // on lv[l].b, lv[l].x

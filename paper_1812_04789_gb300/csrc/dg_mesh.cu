@@ -414,6 +414,7 @@ extern "C" dg_status dg_mesh_create(const dg_mesh_desc* desc, const dg_physics* 
   if (cudaGetDevice(&dev) != cudaSuccess) return DG_ERR_CUDA;
   dg_mesh h = new dg_mesh_s();
   dg_status s = build_mesh(h->m, desc, phys);
+  if (s == DG_OK) s = noalloc_prepare();
   if (s != DG_OK) {
     free_mesh(h->m);
     delete h;

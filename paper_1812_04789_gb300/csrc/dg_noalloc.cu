@@ -5,17 +5,24 @@
 // memory up front, or a time-critical loop that must not enter the CUDA
 // allocator (it may synchronise the device or take a global lock).  This entry
 // point serves them.  It computes exactly what dg_residual computes, with the
-// same kernels, but the face-slot scratch lives in one file-scope device array
-// of fixed size that exists from the moment the library is loaded, instead of
-// in the mesh handle.
+// same face kernel and (for the total-degree space P_p) the same volume
+// kernel, but the face-slot scratch lives in one file-scope device array of
+// fixed size instead of in the mesh handle.  The array belongs to this file's
+// device module, which the CUDA runtime may load lazily (on first use):
+// dg_mesh_create looks the array up on its device, so the module and the
+// array are in place before any mesh handle exists, and a call here finds
+// them without any allocation.
 //
 // Limits and rules:
 //  - the scratch holds NOALLOC_MAX_SLOTS doubles (8 MiB); a mesh needing more
 //    (E * d * 2 * m * n_m doubles) is rejected with DG_ERR_INVALID;
 //  - every GPU that loads the library reserves that array until the process exits;
-//  - the first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture;
+//  - dg_mesh_create looks up the array's device address (cudaGetSymbolAddress)
+//    on its current device, once per device; a device whose first mesh handle
+//    cannot load the array fails there with DG_ERR_OOM, not here;
+//  - on a mesh of the tensor-product space Q_p, dg_residual evaluates the
+//    volume term by sum factorisation and this entry point by the direct
+//    contractions: the two results agree to rounding, not bit for bit;
 //  - all calls share the array: calls that can overlap on the GPU (different
 //    streams without ordering between them) race; order them on one stream;
 //  - the array keeps the last call's contents; no part of it needs to start
@@ -40,7 +47,9 @@ dg_status slots_address(double** out) {
   std::lock_guard<std::mutex> g(g_lock);
   if (!g_addr[dev]) {
     double* p = nullptr;
-    if (cudaGetSymbolAddress((void**)&p, g_noalloc_slots) != cudaSuccess || !p) return DG_ERR_CUDA;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_slots);
+    if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+    if (e != cudaSuccess || !p) return DG_ERR_CUDA;
     g_addr[dev] = p;
   }
   *out = g_addr[dev];
@@ -48,6 +57,15 @@ dg_status slots_address(double** out) {
 }
 
 }  // namespace
+
+namespace dgk {
+// Called by dg_mesh_create on the handle's device: loads the array (and the
+// module that holds it) while allocation is still allowed.
+dg_status noalloc_prepare() {
+  double* p = nullptr;
+  return slots_address(&p);
+}
+}  // namespace dgk
 
 extern "C" dg_status dg_residual_noalloc(dg_mesh mesh, const double* W, const double* S, double* R,
                                          void* stream) {
@@ -59,6 +77,7 @@ extern "C" dg_status dg_residual_noalloc(dg_mesh mesh, const double* W, const do
   double* slots = nullptr;
   dg_status s = slots_address(&slots);
   if (s != DG_OK) return s;
-  if (dgk::launch_residual_with_slots(M, W, S, R, slots, (cudaStream_t)stream) != cudaSuccess) return DG_ERR_CUDA;
-  return DG_OK;
+  const cudaError_t e = dgk::launch_residual_with_slots(M, W, S, R, slots, (cudaStream_t)stream);
+  if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+  return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }

@@ -27,7 +27,12 @@
 //
 // Every wait is bounded: a wait that runs out sets ST_TIMEOUT in the status
 // word, and the CTA leaves its loops together with the others (the decision
-// is taken at a block-wide barrier), frees its TMEM and returns.
+// is taken at a block-wide barrier before the buffer the MMAs read is written
+// again), waits once more, bounded, for the MMAs it issued, frees its TMEM and
+// returns.  If that second wait runs out as well, MMAs may still write the
+// freed TMEM columns: the blocks of a handle whose status shows ST_TIMEOUT,
+// and every tensor-core probe on the device after it, are untrusted until the
+// stream is synchronised and the handle is set up again.
 #include <algorithm>
 #include <vector>
 
@@ -265,8 +270,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int b = ks & 1;
             bool late = false;
             if (issued[b] > waited[b]) {   // the MMAs that last read buffer b
-              late = !mbar_wait(&mbar[b], (issued[b] - 1u) & 1u, TC_WAIT_LIMIT);
-              waited[b] = issued[b];
+              if (mbar_wait(&mbar[b], (issued[b] - 1u) & 1u, TC_WAIT_LIMIT))
+                waited[b] = issued[b];
+              else
+                late = true;
+            }
+            // decided by the whole CTA before buffer b is written again: after a
+            // wait that ran out, no thread touches operands the MMAs may still read
+            if (__syncthreads_or(late)) {
+              if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+              goto done;
             }
             {
               const float4* src = reinterpret_cast<const float4*>(trial + (size_t)((ubase + c0) / 2 + kk) * bufB);
@@ -284,10 +297,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         nm, nmp);
             }
             fence_proxy_async();
-            if (__syncthreads_or(late)) {
-              if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-              goto done;
-            }
+            __syncthreads();
             if (threadIdx.x == 0) {
               fence_after_sync();
               const float* Ab = A + b * bufA;
@@ -312,8 +322,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool late = false;
         for (int b = 0; b < 2; ++b)
           if (issued[b] > waited[b]) {
-            late = late || !mbar_wait(&mbar[b], (issued[b] - 1u) & 1u, TC_WAIT_LIMIT);
-            waited[b] = issued[b];
+            if (mbar_wait(&mbar[b], (issued[b] - 1u) & 1u, TC_WAIT_LIMIT))
+              waited[b] = issued[b];
+            else
+              late = true;
           }
         if (__syncthreads_or(late)) {
           if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
@@ -343,6 +355,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
   }
 done:
+  // after a wait that ran out, MMAs may still be in flight: wait for them once
+  // more (bounded) before the TMEM they write is freed for the next CTA
+  for (int b = 0; b < 2; ++b)
+    if (issued[b] > waited[b] && mbar_wait(&mbar[b], (issued[b] - 1u) & 1u, TC_WAIT_LIMIT)) waited[b] = issued[b];
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, (uint32_t)P.tmem_cols);

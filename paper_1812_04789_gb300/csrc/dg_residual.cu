@@ -473,7 +473,7 @@ static size_t vol_smem(const Mesh& M, int epc, bool jvp) {
 
 template <int D, class T, bool JVP>
 static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T* S, T sigma, T* out,
-                                cudaStream_t st, const T* Pv, const T* Pf) {
+                                cudaStream_t st, const T* Pv, const T* Pf, int parts) {
   MeshView<T> mv = Ms.view<T>();
   Phys<T> ph = Ms.phys_t<T>();
   T* slots = std::is_same<T, double>::value ? (T*)Ms.t64.slots : (T*)Ms.t32.slots;
@@ -483,11 +483,14 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
   if (fsm > 48 * 1024)
     allow_max_smem(face_kernel<D, T, JVP>);
   int nfaces = D * Ms.E;
-  note_launch();
-  face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc,
-                                                                    JVP ? Pf : nullptr);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (parts & 1) {
+    note_launch();
+    face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc,
+                                                                      JVP ? Pf : nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (!(parts & 2)) return cudaSuccess;
   if (Ms.desc.space == DG_SPACE_Q) {   // sum factorisation when it fits
     cudaError_t eq = launch_volume_q<T>(Ms, W, V, S, sigma, JVP, out, st);
     if (eq != cudaErrorNotSupported) return eq;
@@ -522,19 +525,19 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
 
 template <class T>
 cudaError_t launch_residual(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
-                            cudaStream_t st, const T* Pv, const T* Pf) {
+                            cudaStream_t st, const T* Pv, const T* Pf, int parts) {
   if (M.kind == DG_MESH_TRI) return launch_residual_tri<T>(M, W, V, S, sigma, jvp, out, st);
   if (M.d == 2)
-    return jvp ? run_residual<2, T, true>(M, W, V, S, sigma, out, st, Pv, Pf)
-               : run_residual<2, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr);
-  return jvp ? run_residual<3, T, true>(M, W, V, S, sigma, out, st, Pv, Pf)
-             : run_residual<3, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr);
+    return jvp ? run_residual<2, T, true>(M, W, V, S, sigma, out, st, Pv, Pf, parts)
+               : run_residual<2, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr, parts);
+  return jvp ? run_residual<3, T, true>(M, W, V, S, sigma, out, st, Pv, Pf, parts)
+             : run_residual<3, T, false>(M, W, V, S, sigma, out, st, nullptr, nullptr, parts);
 }
 
 template cudaError_t launch_residual<double>(const Mesh&, const double*, const double*, const double*, double,
-                                             bool, double*, cudaStream_t, const double*, const double*);
+                                             bool, double*, cudaStream_t, const double*, const double*, int);
 template cudaError_t launch_residual<float>(const Mesh&, const float*, const float*, const float*, float, bool,
-                                            float*, cudaStream_t, const float*, const float*);
+                                            float*, cudaStream_t, const float*, const float*, int);
 
 // Primal traces of the FP32 state at every volume point, Pv[e][q] = (u, grad u),
 // and at every face point on both sides, Pf[f][q][side] (face f = k E + e joins

@@ -102,6 +102,8 @@ size_t estimate_bytes(const Key& k) {
     long nb = m * nmodes(k.opts.p_level[l]);
     const long ld = (nb + (long)(16 / es) - 1) / (long)(16 / es) * (long)(16 / es);   // padded inverse rows
     bytes += (size_t)E * nb * ld * es * (l == 0 ? 1 : 2 + 2 * d.dim);   // inverse (+ coarse D and O)
+    if (k.opts.block_storage == DG_STORE_BF16)                          // their BF16 copies
+      bytes += (size_t)E * nb * ((nb + 7) / 8 * 8) * 2 * (l == 0 ? 1 : 2 + 2 * d.dim);
     int nu = l == nl - 1 ? k.opts.nu_coarse : std::max(k.opts.nu_pre[l], k.opts.nu_post[l]);
     bytes += (size_t)E * nb * es * (2 * nu + 8);
   }

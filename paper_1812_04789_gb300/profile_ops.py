@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--n", type=int, nargs="*", default=None, help="override the mesh size")
+    ap.add_argument("--bf16", action="store_true", help="BF16 block storage (mixed precision)")
+    ap.add_argument("--dt", type=float, default=None, help="override the time step (convective units)")
     a = ap.parse_args()
     import torch
     from paper_1812_04789_gb300 import binding as B
@@ -36,6 +38,8 @@ def main():
     cfg = dict(wl.CONFIGS[a.config])
     if a.n:
         cfg["n"] = tuple(a.n) + (1,) * (3 - len(a.n))
+    if a.dt:
+        cfg["dt_conv"] = a.dt
     prec = B.PREC_MIXED if a.precision == "mixed" else B.PREC_FP64
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
@@ -46,11 +50,13 @@ def main():
         v = torch.randn_like(W)
         out = torch.empty_like(W)
         pl = cfg["p_levels"]
-        o = B.pmg_opts(pl, 10, 10, 30, cycle=B.CYCLE_FMG if len(pl) > 1 else B.CYCLE_BJ, precision=prec)
+        o = B.pmg_opts(pl, 10, 10, 30, cycle=B.CYCLE_FMG if len(pl) > 1 else B.CYCLE_BJ, precision=prec,
+                       storage=B.STORE_BF16 if a.bf16 else B.STORE_NATIVE)
         pmg = B.PMG(m, W, sigma, o, stream=st) if a.op in ("apply", "refresh", "fgmres", "step") else None
         bj = None
         if a.op == "bj":
-            bj = B.PMG(m, W, sigma, B.pmg_opts((cfg["p"],), cycle=B.CYCLE_BJ, precision=prec), stream=st)
+            bj = B.PMG(m, W, sigma, B.pmg_opts((cfg["p"],), cycle=B.CYCLE_BJ, precision=prec,
+                                               storage=B.STORE_BF16 if a.bf16 else B.STORE_NATIVE), stream=st)
         b = torch.empty_like(W)
         m.bdf2_rhs(W, W, W, dt, b, stream=st)
         Wk = torch.empty_like(W)
@@ -87,7 +93,11 @@ def main():
             op()
         e1.record(st)
         e1.synchronize()
-        print(json.dumps({"op": a.op, "precision": a.precision, "config": a.config, "n": cfg["n"],
+        its = None
+        if a.op in ("fgmres", "step"):
+            its = pmg.fgmres(W, b, out, stream=st)["iters"]
+        print(json.dumps({"op": a.op, "precision": a.precision, "config": a.config, "n": cfg["n"], "bf16": a.bf16,
+                          "iters": its,
                           "ms_per_rep": e0.elapsed_time(e1) / a.reps,
                           "launches_per_rep": (B.launch_count() - l0) / a.reps}))
 

@@ -6,8 +6,12 @@ time-critical loop kept out of the CUDA allocator) call dg_residual_noalloc,
 which keeps its face scratch in a fixed device array inside the library.  This
 test calls it through the C ABI twice in a row and checks each result against
 dg_residual (same kernels, so within the residual tolerance of the parity
-tests, 1e-12 relative max-norm), and that an oversized mesh is refused.  The
-file is collected last so that a failure here leaves every other test run.
+tests, 1e-12 relative max-norm), including a mesh of the tensor-product space
+Q_p (where dg_residual sums the volume term by factorisation and this entry
+point takes the direct contractions: equal to rounding); that repeated calls
+leave the device's free memory unchanged and launch only the face and volume
+kernels; and that an oversized mesh is refused.  The file is collected last
+so that a failure here leaves every other test run.
 """
 import numpy as np
 import pytest
@@ -26,7 +30,8 @@ def _relmax(a, b):
 
 
 @pytest.mark.parametrize("cfg", [wl.make_config("tgv", 3, (5, 4, 3), 3, M=0.2, Re=400.0),
-                                 wl.make_config("vortex", 2, (9, 7), 2, M=0.5, Re=1000.0)])
+                                 wl.make_config("vortex", 2, (9, 7), 2, M=0.5, Re=1000.0),
+                                 wl.make_config("tgv", 3, (3, 4, 3), 3, M=0.2, Re=400.0, space="Q")])
 def test_noalloc_matches_residual_twice(cfg):
     build.build()
     assert torch.cuda.is_available()
@@ -41,6 +46,25 @@ def test_noalloc_matches_residual_twice(cfg):
         torch.cuda.synchronize()
         assert _relmax(got, ref) <= 1e-12
         assert torch.isfinite(got).all()
+
+
+def test_noalloc_calls_allocate_nothing():
+    """After one call, further calls leave the driver's free-memory count as
+    it was, and each launches exactly the face and the volume kernel."""
+    build.build()
+    cfg = wl.make_config("tgv", 3, (6, 5, 4), 3, M=0.2, Re=400.0)
+    m = B.Mesh.from_workload(wl.mesh_desc(cfg), wl.physics(cfg))
+    W = torch.from_numpy(wl.perturbed_state(cfg, amp=0.05)).cuda()
+    R = torch.empty_like(W)
+    m.residual_noalloc(W, R)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    l0 = B.launch_count()
+    for _ in range(5):
+        m.residual_noalloc(W, R)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert B.launch_count() - l0 == 5 * 2
 
 
 def test_noalloc_rejects_meshes_beyond_the_cap():
