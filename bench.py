@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-bilu", action="store_true")
     ap.add_argument("--no-triangles", action="store_true")
     ap.add_argument("--no-qspace", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-large-dt", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--c3-fp64", type=int, default=1, help="FP64 steps of the 32^3 p=6 case (0: skip)")
     return ap.parse_args()
 
 
@@ -111,7 +115,7 @@ class Clocks:
 class Stepper:
     """One BDF2 implicit step on the device through the library's C ABI."""
 
-    def __init__(self, B, torch, cfg, precision, stream, W0, Wm1, coarse=0, order=0):
+    def __init__(self, B, torch, cfg, precision, stream, W0, Wm1, coarse=0, order=0, storage=0):
         self.B, self.torch = B, torch
         self.cfg = cfg
         self.stream = stream
@@ -122,7 +126,7 @@ class Stepper:
         o = bench_opts(cfg)
         self.opts = B.pmg_opts(o["p_levels"], nu_pre=o["nu_pre"], nu_post=o["nu_post"],
                                nu_coarse=o["nu_coarse"], cycle=o["cycle"], precision=precision,
-                               coarse=coarse, order=order)
+                               coarse=coarse, order=order, storage=storage)
         dev = torch.device("cuda", torch.cuda.current_device())
         self.W0 = torch.from_numpy(W0).to(dev)
         self.Wm1 = torch.from_numpy(Wm1).to(dev)
@@ -334,6 +338,48 @@ def q_space_jvp(torch, B, stream, n=10):
         return {"error": "%s: %s" % (type(exc).__name__, exc)}
 
 
+def variant_steps(torch, B, cfg, stream, newton, flush, runs, W0=None, Wm1=None, ref_final=None):
+    """One workload in several preconditioner variants: for each (name,
+    precision, storage, warm-up, timed steps) in `runs`, BDF2 steps from the same
+    (W^n, W^{n-1}) on a fresh handle; device time per step, DOFs/s, FGMRES
+    iterations per solve, and W^{n+1} against the FP64 variant when present
+    (relative L2 of W^{n+1} and of the step dW).  A failing variant is reported
+    as such and the others stand."""
+    if W0 is None:
+        W0 = wl.initial_state(cfg)
+        Wm1 = wl.initial_state(cfg, t=-wl.time_step(cfg)) if cfg["case"] == "vortex" else W0
+    out, finals = {}, {}
+    for name, prec, storage, warm, steps in runs:
+        st = None
+        try:
+            st = Stepper(B, torch, cfg, prec, stream, W0, Wm1, storage=storage)
+            times = timed_steps(torch, st, steps, warm, newton, stream, flush)
+            ms = statistics.mean(times)
+            out[name] = {"ms_per_step": ms, "value": st.ndofs / (ms * 1e-3), "unit": UNIT,
+                         "fgmres_iters_per_solve": statistics.mean(st.iters), "steps": steps,
+                         "warmup": warm}
+            finals[name] = st.Wk.cpu().numpy()
+        except Exception as exc:
+            out[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        finally:
+            if st is not None:
+                st.pmg.close()
+                st.mesh.close()
+            torch.cuda.empty_cache()
+    ref = finals.get("fp64", ref_final)
+    if ref is not None:
+        for name, W in finals.items():
+            if name != "fp64":
+                out[name]["vs_fp64_rel_l2"] = float(np.linalg.norm(W - ref) / np.linalg.norm(ref))
+                out[name]["vs_fp64_dW_rel_l2"] = float(np.linalg.norm(W - ref) / max(np.linalg.norm(ref - W0), 1e-300))
+    out["dofs"] = int(W0.size)
+    out["workload"] = "TGV %dx%dx%d hex, p=%d, Re=%g, M=%g, BDF2 dt=%g t_c, pMG %s FMG nu=10/10/30, " \
+                      "FGMRES(30) rtol 1e-5, %d Newton/step" % (*cfg["n"], cfg["p"], cfg["Re"], cfg["M"],
+                                                                cfg["dt_conv"], "-".join(map(str, cfg["p_levels"])),
+                                                                newton)
+    return out
+
+
 def kernel_roofline(torch, B, stepper, stream, peaks):
     """Average duration of the fine-level block-Jacobi apply (the HBM-bound
     kernel that streams every inverse diagonal block once) and of the FP64 JVP
@@ -404,6 +450,101 @@ def kernel_roofline(torch, B, stepper, stream, peaks):
                                peak_source="measured bf16 burst x nominal TF32/BF16 ratio 1.1/2.25")
         del D
     return out
+
+
+# Peaks for the ALU-bound kernels, from the unit counts and the maximum SM
+# clock (the measured peaks cover HBM and the BF16 tensor pipe only):
+# FP32: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; FP64: GB300's
+# nominal 1.25 TFLOP/s (152 SMs x 2 DFMA lanes x 2 flop x 2.07 GHz = 1.26).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def kernel_rooflines(torch, B, mixed, fp64, stream, peaks, ref_cfg):
+    """Rooflines of the kernels that own the implicit step, each timed alone
+    with dg_pmg_kernel_time (CUDA events on the library's stream, 10 launches
+    after the handle's own set-up).  Work per launch:
+      * ALU-bound JVP kernels: the floating-point operations the kernel executes
+        per element, counted by ncu (FADD/FMUL 1, FFMA 2, paired ops twice;
+        profiles/kernel_work.json, from one capture of each kernel) times E;
+        traffic: DRAM bytes per element of the same capture times E;
+      * HBM-bound kernels: the algorithmic bytes (blocks streamed once per
+        product, vectors read or written once).
+    Returns a list, the kernels ordered by the share of the step that the
+    launch list of a step gives them (profiles/)."""
+    work = {}
+    wf = os.path.join(ROOT, "profiles", "kernel_work.json")
+    if os.path.exists(wf):
+        work = json.load(open(wf))
+    E, nb = mixed.mesh.E, mixed.mesh.m * mixed.mesh.nm
+    out = []
+
+    def alu(name, handle, kt, key, peak, dtype):
+        ms = handle.pmg.kernel_time(kt, 0, 10, stream=stream)
+        rec = work.get(key, {})
+        same = rec.get("config") == ref_cfg
+        fl = rec.get("flops_per_element")
+        tr = rec.get("dram_bytes_per_element")
+        ach = fl * E / (ms * 1e-3) / 1e12 if (fl and same) else None
+        out.append({"kernel": name, "bound": "alu", "dtype": dtype, "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak if ach else None,
+                    "traffic": int(tr * E) if (tr and same) else None, "ms": ms,
+                    "flops": fl * E if (fl and same) else None,
+                    "peak_source": "nominal: unit counts x 2.07 GHz max SM clock",
+                    "work_source": "executed FP ops per element (ncu, profiles/kernel_work.json)"})
+
+    alu("face_kernel<3,float,1> (smoother JVP, faces; FP32 with cached traces)", mixed, B.KT_FACE_JVP,
+        "face_jvp_fp32", FP32_PEAK_TFLOPS, "f32")
+    alu("volume_kernel_st<3,1,3> (smoother JVP, volume; FP32, tables in shared memory)", mixed, B.KT_VOLUME_JVP,
+        "volume_jvp_fp32", FP32_PEAK_TFLOPS, "f32")
+    if fp64 is not None:
+        alu("face_kernel<3,double,1> (outer JVP, faces; FP64)", fp64, B.KT_FACE_JVP, "face_jvp_fp64",
+            FP64_PEAK_TFLOPS, "f64")
+        alu("volume_kernel<3,double,1> (outer JVP, volume; FP64)", fp64, B.KT_VOLUME_JVP, "volume_jvp_fp64",
+            FP64_PEAK_TFLOPS, "f64")
+    # block-Jacobi apply of the fine level (FP32 inverses, column-major, padded rows)
+    ld = (nb + 3) // 4 * 4
+    ms = mixed.pmg.kernel_time(B.KT_BLOCK_JACOBI, 0, 20, stream=stream)
+    by = E * (nb * ld * 4 + 2 * nb * 4)
+    out.append({"kernel": "bj_colmajor_kernel<float> (fine block-Jacobi apply)", "bound": "hbm", "dtype": "f32",
+                "achieved": by / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": by / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None, "ms": ms,
+                "algorithmic_bytes": by})
+    # persistent smoother of level 1 (p = 2): its HBM traffic is the inherited
+    # blocks (diagonal + 2d neighbours) of every product and the inverse
+    # diagonal blocks of every block-Jacobi apply; the Krylov basis stays on chip
+    nl = len(mixed.cfg["p_levels"])
+    if nl > 1:
+        p1 = mixed.cfg["p_levels"][1]
+        nb1 = mixed.mesh.m * wl.n_modes(p1, len(mixed.cfg["n"]))
+        ld1 = (nb1 + 3) // 4 * 4
+        nu = 10 if nl > 2 else 30
+        ms = mixed.pmg.kernel_time(B.KT_SMOOTH, 1, 5, stream=stream)
+        nf = 2 * len(mixed.cfg["n"])
+        by = E * nb1 * ld1 * 4 * ((nu + 1) * (1 + nf) + nu) + E * nb1 * 4 * (4 + 2 * nu)
+        out.append({"kernel": "coop_smooth_kernel<float> (one smoother call, level 1, %d iterations)" % nu,
+                    "bound": "hbm", "dtype": "f32", "achieved": by / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": by / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                    "ms": ms, "algorithmic_bytes": by})
+    return out
+
+
+def dominant_roofline(roofs):
+    """The roofline entry of the kernel with the largest share of a mixed step:
+    the share each kernel has in the committed launch list of one step
+    (profiles/step_shares.json, from ncu gpu__time_duration of every launch)."""
+    shares = {}
+    sf = os.path.join(ROOT, "profiles", "step_shares.json")
+    if os.path.exists(sf):
+        shares = json.load(open(sf)).get("shares", {})
+    best, best_share = None, -1.0
+    for r in roofs:
+        key = r["kernel"].split(" ")[0]
+        sh = shares.get(key, 0.0)
+        r["share_of_step"] = sh
+        if sh > best_share:
+            best, best_share = r, sh
+    return dict(best) if best else None
 
 
 def batched_sample(B, count=64, workers=8, budget=120 << 30):
@@ -558,12 +699,14 @@ def run_gb300(args):
     Wm1 = wl.initial_state(cfg, t=-wl.time_step(cfg)) if cfg["case"] == "vortex" else W0
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     results = {}
+    steppers = {}
     with torch.cuda.stream(stream):
         clocks = Clocks(local)
         for name, prec, steps in (("mixed", B.PREC_MIXED, args.steps), ("fp64", B.PREC_FP64, args.fp64_steps)):
             if steps <= 0:
                 continue
             st = Stepper(B, torch, cfg, prec, stream, W0, Wm1)
+            steppers[name] = st
             if name == "mixed":
                 clocks.start()
                 l0 = B.launch_count()
@@ -584,6 +727,34 @@ def run_gb300(args):
             err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
             err_dw = float(np.linalg.norm(a - b) / max(np.linalg.norm(b - W0), 1e-300))
         roof = kernel_roofline(torch, B, head, stream, peaks)
+        roofs = kernel_rooflines(torch, B, head, steppers.get("fp64"), stream, peaks, args.config)
+        if "fp64" in steppers:
+            steppers["fp64"].pmg.close()
+            del steppers["fp64"]
+            torch.cuda.empty_cache()
+        # BF16 block storage on the headline case (same steps as the headline)
+        bf16 = None
+        if not args.no_bf16:
+            bf16 = variant_steps(torch, B, cfg, stream, args.newton, flush,
+                                 [("mixed_bf16", B.PREC_MIXED, B.STORE_BF16, 2, max(1, min(args.steps, 5)))],
+                                 W0=W0, Wm1=Wm1, ref_final=results.get("fp64", {}).get("Wfinal"))["mixed_bf16"]
+        # the headline case at a large time step (dt = 1 t_c, the paper's vortex runs at dt = 1):
+        # the preconditioner has to work here, mixed vs FP64 iterations and states
+        large = None
+        if not args.no_large_dt:
+            cl = dict(cfg)
+            cl["dt_conv"] = 1.0
+            large = variant_steps(torch, B, cl, stream, args.newton, flush,
+                                  [("fp64", B.PREC_FP64, 0, 0, 1), ("mixed", B.PREC_MIXED, 0, 1, 2),
+                                   ("mixed_bf16", B.PREC_MIXED, B.STORE_BF16, 1, 2)])
+        # the stiff large case the mixed precision is meant for: TGV 32^3, p = 6, M = 0.05
+        c3 = None
+        if not args.no_c3:
+            runs = [("mixed", B.PREC_MIXED, 0, 1, 1), ("mixed_bf16", B.PREC_MIXED, B.STORE_BF16, 1, 1)]
+            if args.c3_fp64 > 0:
+                runs.insert(0, ("fp64", B.PREC_FP64, 0, 0, args.c3_fp64))
+            c3 = variant_steps(torch, B, wl.CONFIGS["tgv32_p6"], stream, args.newton, flush, runs)
+            c3["note"] = "FP64 timed without a warm-up step (one step takes about a minute); mixed after one"
         esd = None if args.no_esdirk else esdirk3_steps(torch, B, head, max(1, min(args.steps, 3)), args.newton,
                                                         stream, flush)
         bilu = None if args.no_bilu else coarse_bilu_steps(torch, B, cfg, stream, W0, Wm1, args.newton, flush)
@@ -633,7 +804,9 @@ def run_gb300(args):
                  "fgmres_iters_per_solve": results.get("fp64", {}).get("fgmres_iters_per_solve")},
         "fgmres_iters_per_solve": mixed["fgmres_iters_per_solve"],
         "mixed_vs_fp64_rel_l2": err, "mixed_vs_fp64_dW_rel_l2": err_dw,
-        "roofline": {"bound": "hbm",
+        "roofline": dominant_roofline(roofs),
+        "rooflines": roofs,
+        "bj_apply_with_conversions": {"bound": "hbm",
                      "kernel": "bj_colmajor_kernel<float> (fine block-Jacobi apply; timed with the FP64<->FP32 "
                                "conversions of its input and output, whose bytes are counted)",
                      "achieved": bj["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -642,6 +815,9 @@ def run_gb300(args):
                      "ms": bj["ms"], "algorithmic_bytes": bj["bytes"]},
         "jvp_fp64": roof["jvp_fp64"],
         "probe_tc": roof.get("probe_tc"),
+        "mixed_bf16": bf16,
+        "large_dt": large,
+        "tgv32_p6": c3,
         "esdirk3": esd,
         "coarse_bilu": bilu,
         "triangles": tris,

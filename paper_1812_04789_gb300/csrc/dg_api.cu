@@ -264,7 +264,7 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
         L.coop.nu_max = nmax;
         CK(dalloc(mg.allocs, (void**)&L.cpart, sizeof(double) * (size_t)L.coop.grid * (2 * (nmax + 1) + 1),
                   &h->vector_bytes));
-        CK(dalloc(mg.allocs, (void**)&L.cbar, sizeof(unsigned) * 4, &h->vector_bytes));
+        CK(dalloc(mg.allocs, (void**)&L.cbar, sizeof(unsigned) * COOP_BAR_WORDS, &h->vector_bytes));
       }
     }
   }

@@ -279,10 +279,11 @@ struct CoopPlan {
   size_t smem = 0;
 };
 cudaError_t plan_coop_smoother(int bf16, int nb, int nf, int E, int nu, CoopPlan* plan);
+constexpr int COOP_BAR_WORDS = 64;   // barrier words per level (arrivals at 0, release at 32)
 // One SMOOTH call (nu GMRES(BJ) iterations from x on A x = b, Algorithm 2) in
 // one cooperative launch: FP32 vectors, blocks column-major in FP32 (inv_ld)
 // or, when Dinv16 is given, BF16 (ld_bf16).  part: grid * (2 (nu_max + 1) + 1)
-// doubles; bar: one counter (zeroed by the call, on the stream); a bounded
+// doubles; bar: COOP_BAR_WORDS words (zeroed by the call, on the stream); a bounded
 // grid barrier that runs out sets ST_TIMEOUT in *status.  expect_extra > 0
 // makes every barrier wait for CTAs that do not exist (the wait then runs out).
 cudaError_t launch_coop_smoother(const CoopPlan& pl, const float* Dinv, const float* Dop, const float* O,

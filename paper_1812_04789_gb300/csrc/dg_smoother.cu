@@ -4,9 +4,13 @@
 // on the inherited block-sparse operator of Sec. 6.1), where the
 // launch-per-operation path takes about eleven small kernels per iteration.
 //
-// Work split: CTA c owns a contiguous range of elements for the whole call
-// (its rows of every vector).  Per iteration j:
-//   A  v_j = w / ||w|| (own rows); z_j = D^{-1} v_j (own elements)      | grid barrier
+// One CTA per SM owns a contiguous range of elements for the whole call and
+// keeps its rows of the Krylov basis V, of the preconditioned directions Z and
+// of the work vector w in shared memory (the coarse levels are small: a level
+// whose rows do not fit keeps the launch-per-operation smoother).  Only z_j
+// goes to device memory, where the neighbours' products read it.  Per
+// iteration j:
+//   A  v_j = w / ||w||; z_j = D^{-1} v_j (own elements)                 | grid barrier
 //   B  w = A z_j (own elements, neighbours' z_j read); partial V^T w    | grid barrier
 //   C  h1 = sum of partials; w -= V h1; partial V^T w                    | grid barrier
 //   D  h2 = sum of partials; w -= V h2; partial ||w||^2                  | grid barrier
@@ -15,8 +19,9 @@
 // Hessenberg matrix, the Givens rotations and g, so all CTAs hold identical
 // scalars and the final x += Z y needs no further barrier.
 //
-// The grid barrier is a counter in device memory, zeroed before the launch:
-// barrier k waits until k * expect CTAs have arrived.  Every wait is bounded
+// The grid barrier counts arrivals in one word and releases the waiting CTAs
+// through another (its own 128-byte line, so the polls do not contend with
+// the arrivals); both are zeroed before the launch.  Every wait is bounded
 // (2 s of the global timer): on expiry the CTA sets ST_TIMEOUT in the mesh
 // status word and returns, and the other CTAs see the flag while they wait
 // and return too; a launch that finds ST_TIMEOUT already set returns at once.
@@ -57,16 +62,16 @@ struct CoopArgs {
   const int* nbr;       // [E][nf]
   const float* b;
   float* x;
-  float* V;             // (nu + 1) x N
-  float* Z;             // nu x N
-  float* w;             // N
+  float* Z;             // nu x N: the directions z_j, read by the neighbours' products
   double* part;         // [grid][2 (nu + 1) + 1]
-  unsigned* bar;        // barrier counter, zero at launch
+  unsigned* bar;        // [0]: arrivals, [32]: released barrier number; zero at launch
   int* status;          // mesh status word (ST_TIMEOUT)
   int* kflag;           // Krylov status bits (ST_NONFINITE)
   long N;
   int nu, nb, ld, nf, E, chunk, epc, tpe, expect;
 };
+
+constexpr int COOP_THREADS = 512;
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -74,26 +79,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier number k (target k * expect arrivals); false when a wait
-// ran out here or elsewhere (ST_TIMEOUT), and then the caller returns.
-__device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, int* sflag) {
+// Grid-wide barrier number k (k * expect arrivals); false when a wait ran out
+// here or elsewhere (ST_TIMEOUT), and then the caller returns.
+__device__ bool grid_barrier(unsigned* bar, unsigned k, unsigned expect, int* status, int* sflag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    const unsigned long long t0 = global_ns();
     int ok = 1;
-    while (*(volatile unsigned*)bar < target) {
-      if (*(volatile int*)status & ST_TIMEOUT) {
-        ok = 0;
-        break;
+    __threadfence();
+    const unsigned old = atomicAdd(bar, 1u);
+    if (old + 1u == k * expect) {
+      __threadfence();
+      atomicExch(bar + 32, k);            // the last arrival releases barrier k
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*(volatile unsigned*)(bar + 32) < k) {
+        if (*(volatile int*)status & ST_TIMEOUT) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > 2000000000ull) {
+          atomicOr(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
       }
-      if (global_ns() - t0 > 2000000000ull) {
-        atomicOr(status, ST_TIMEOUT);
-        ok = 0;
-        break;
-      }
-      __nanosleep(32);
     }
     __threadfence();
     *sflag = ok;
@@ -102,7 +112,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned target, int* status, int* s
   return *sflag != 0;
 }
 
-// sum over the CTA's threads of s, returned to every thread (red: 32 doubles)
+// sum over the CTA's threads of s, valid in every thread (red: 32 doubles)
 __device__ double block_sum(double s, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -115,13 +125,13 @@ __device__ double block_sum(double s, double* red) {
   return t;
 }
 
-// out[i] = sum over the CTA's rows [n0, n1) of V_i . w, i < nv (warp per i)
-__device__ void own_dots(int nv, const float* V, long N, const float* w, long n0, long n1, double* out) {
+// out[i] = sum over the CTA's rows of V_i . w (shared memory), i < nv, warp per i
+__device__ void own_dots(int nv, const float* Vs, int ldv, const float* ws, int rows, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < nv; i += nw) {
-    const float* v = V + (size_t)i * N;
+    const float* v = Vs + (size_t)i * ldv;
     double s = 0.0;
-    for (long n = n0 + lane; n < n1; n += 32) s += (double)v[n] * (double)w[n];
+    for (int r = lane; r < rows; r += 32) s += (double)v[r] * (double)ws[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[i] = s;
@@ -129,12 +139,22 @@ __device__ void own_dots(int nv, const float* V, long N, const float* w, long n0
 }
 
 // dst[i] = sum over CTAs c = 0..G-1 of part[c * stride + i], i < nv, in a
-// fixed order (the same in every CTA); partials of other CTAs read past L1
+// fixed order (the same in every CTA); other CTAs' partials read past L1,
+// eight loads in flight per lane
 __device__ void sum_parts(int nv, const double* part, int stride, int G, double* dst) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < nv; i += nw) {
     double s = 0.0;
-    for (int c = lane; c < G; c += 32) s += __ldcg(part + (size_t)c * stride + i);
+    for (int c0 = lane; c0 < G; c0 += 8 * 32) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = c0 + 32 * u;
+        t[u] = c < G ? __ldcg(part + (size_t)c * stride + i) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += t[u];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) dst[i] = s;
@@ -142,70 +162,65 @@ __device__ void sum_parts(int nv, const double* part, int stride, int G, double*
   __syncthreads();
 }
 
-// out_e = [bsub_e -] (D_e in_e + sum_s O_{e,s} in_nbr(e,s)) for e in [e_beg, e_end):
-// a thread per (element, block, R rows), partial rows summed in a fixed order.
+// ws[own rows of e] = [b_e -] (D_e in_e + sum_s O_{e,s} in_nbr(e,s)) for the
+// CTA's ne elements from e_beg: a thread per (element, R rows) sums all the
+// element's blocks; the inputs are staged in shared memory, epc elements a pass.
 template <class S>
-__device__ void bsr_own(const CoopArgs<S>& a, const float* in, float* out, const float* bsub, int e_beg, int e_end,
-                        float* xs, float* pt) {
+__device__ void bsr_own(const CoopArgs<S>& a, const float* in, const float* bsub, float* ws, int e_beg, int ne,
+                        float* xs) {
   constexpr int R = Col16<S>::R;
-  const int nb = a.nb, ld = a.ld, nf = a.nf, nsrc = 1 + nf, tpb = nsrc * a.tpe;
+  const int nb = a.nb, ld = a.ld, nf = a.nf, nsrc = 1 + nf, tpe = a.tpe, epc = a.epc;
   const size_t bs = (size_t)nb * ld;
-  const int sub = threadIdx.x / tpb, r = threadIdx.x - sub * tpb, blk = r / a.tpe, tt = r - blk * a.tpe;
-  for (int e0 = e_beg; e0 < e_end; e0 += a.epc) {
-    const int nl = min(a.epc, e_end - e0);
+  const int sub = threadIdx.x / tpe, tt = threadIdx.x - sub * tpe;
+  for (int p0 = 0; p0 < ne; p0 += epc) {
+    const int nl = min(epc, ne - p0);
     for (int t = threadIdx.x; t < nl * nsrc * nb; t += blockDim.x) {
       const int el = t / (nsrc * nb), q = t - el * nsrc * nb, who = q / nb, j = q - who * nb;
-      const int e = e0 + el;
+      const int e = e_beg + p0 + el;
       const int src = who == 0 ? e : a.nbr[(size_t)e * nf + who - 1];
       xs[t] = __ldcg(in + (size_t)src * nb + j);
     }
     __syncthreads();
     if (sub < nl) {
-      const int e = e0 + sub;
-      const S* base = (blk == 0 ? a.Dop + (size_t)e * bs : a.O + ((size_t)e * nf + blk - 1) * bs) + R * tt;
-      const float* xb = xs + ((size_t)sub * nsrc + blk) * nb;
+      const int e = e_beg + p0 + sub;
       float acc[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) acc[j] = 0.f;
+      for (int blk = 0; blk < nsrc; ++blk) {
+        const S* base = (blk == 0 ? a.Dop + (size_t)e * bs : a.O + ((size_t)e * nf + blk - 1) * bs) + R * tt;
+        const float* xb = xs + ((size_t)sub * nsrc + blk) * nb;
 #pragma unroll 8
-      for (int c = 0; c < nb; ++c) {
-        float v[R];
-        Col16<S>::load(base + (size_t)c * ld, v);
-        const float xv = xb[c];
+        for (int c = 0; c < nb; ++c) {
+          float v[R];
+          Col16<S>::load(base + (size_t)c * ld, v);
+          const float xv = xb[c];
 #pragma unroll
-        for (int j = 0; j < R; ++j) acc[j] += v[j] * xv;
+          for (int j = 0; j < R; ++j) acc[j] += v[j] * xv;
+        }
       }
-      float* p = pt + ((size_t)sub * nsrc + blk) * ld + R * tt;
+      const int r0 = (p0 + sub) * nb + R * tt;
+      const size_t n0 = (size_t)e_beg * nb;
 #pragma unroll
-      for (int j = 0; j < R; ++j) p[j] = acc[j];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) {
-      const int el = t / nb, row = t - el * nb;
-      const float* pe = pt + (size_t)el * nsrc * ld + row;
-      float s = 0.f;
-      for (int bb = 0; bb < nsrc; ++bb) s += pe[(size_t)bb * ld];
-      const size_t n = (size_t)(e0 + el) * nb + row;
-      out[n] = bsub ? bsub[n] - s : s;
+      for (int j = 0; j < R; ++j)
+        if (R * tt + j < nb) ws[r0 + j] = bsub ? __ldcg(bsub + n0 + r0 + j) - acc[j] : acc[j];
     }
     __syncthreads();
   }
 }
 
-// z_e = D_e^{-1} v_e for e in [e_beg, e_end) (own rows only)
+// z_e = D_e^{-1} v_e for the CTA's elements: v from shared memory, z to shared
+// memory (own rows) and device memory (the neighbours' products read it)
 template <class S>
-__device__ void bj_own(const CoopArgs<S>& a, const float* v, float* z, int e_beg, int e_end, float* xs) {
+__device__ void bj_own(const CoopArgs<S>& a, const float* vs, float* zs, float* zg, int e_beg, int ne) {
   constexpr int R = Col16<S>::R;
   const int nb = a.nb, ld = a.ld, tpe = a.tpe, epc = blockDim.x / tpe;
   const size_t bs = (size_t)nb * ld;
   const int sub = threadIdx.x / tpe, tt = threadIdx.x - sub * tpe;
-  for (int e0 = e_beg; e0 < e_end; e0 += epc) {
-    const int nl = min(epc, e_end - e0);
-    for (int t = threadIdx.x; t < nl * nb; t += blockDim.x) xs[t] = v[(size_t)e0 * nb + t];
-    __syncthreads();
+  for (int p0 = 0; p0 < ne; p0 += epc) {
+    const int nl = min(epc, ne - p0);
     if (sub < nl) {
-      const S* base = a.Dinv + (size_t)(e0 + sub) * bs + R * tt;
-      const float* xe = xs + (size_t)sub * nb;
+      const S* base = a.Dinv + (size_t)(e_beg + p0 + sub) * bs + R * tt;
+      const float* xe = vs + (size_t)(p0 + sub) * nb;
       float acc[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) acc[j] = 0.f;
@@ -217,19 +232,21 @@ __device__ void bj_own(const CoopArgs<S>& a, const float* v, float* z, int e_beg
 #pragma unroll
         for (int j = 0; j < R; ++j) acc[j] += m[j] * xv;
       }
-      float* zo = z + (size_t)(e0 + sub) * nb + R * tt;
+      const int r0 = (p0 + sub) * nb + R * tt;
 #pragma unroll
       for (int j = 0; j < R; ++j)
-        if (R * tt + j < nb) zo[j] = acc[j];
+        if (R * tt + j < nb) {
+          zs[r0 + j] = acc[j];
+          zg[(size_t)e_beg * nb + r0 + j] = acc[j];
+        }
     }
-    __syncthreads();
   }
 }
 
 template <class S>
-__global__ void __launch_bounds__(256) coop_smooth_kernel(CoopArgs<S> a) {
+__global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nu = a.nu, ldh = nu + 1;
+  const int nu = a.nu, ldh = nu + 1, nb = a.nb;
   double* H = reinterpret_cast<double*>(smem_raw);   // (nu + 1) x nu, column-major
   double* cs = H + (size_t)ldh * nu;
   double* sn = cs + nu;
@@ -238,15 +255,18 @@ __global__ void __launch_bounds__(256) coop_smooth_kernel(CoopArgs<S> a) {
   double* h2 = h1 + ldh;                              // nu + 1
   double* red = h2 + ldh;                             // 32
   int* sflag = reinterpret_cast<int*>(red + 32);      // 4 ints
-  float* xs = reinterpret_cast<float*>(sflag + 4);
-  const int nsrc = 1 + a.nf;
-  float* pt = xs + std::max((size_t)a.epc * nsrc * a.nb, (size_t)(blockDim.x / a.tpe) * a.nb);
+  const int rmax = a.chunk * nb;
+  float* Vs = reinterpret_cast<float*>(sflag + 4);    // [nu + 1][rmax]
+  float* Zs = Vs + (size_t)ldh * rmax;                // [nu][rmax]
+  float* ws = Zs + (size_t)nu * rmax;                 // [rmax]
+  float* xs = ws + rmax;                              // [epc][1 + nf][nb]
 
   const int G = gridDim.x, stride = 2 * ldh + 1;
   double* mypart = a.part + (size_t)blockIdx.x * stride;   // [0, ldh): pass 1, [ldh, 2 ldh): pass 2, last: norm
-  const int e_beg = min(a.E, (int)blockIdx.x * a.chunk), e_end = min(a.E, e_beg + a.chunk);
-  const long n0 = (long)e_beg * a.nb, n1 = (long)e_end * a.nb;
+  const int e_beg = min(a.E, (int)blockIdx.x * a.chunk), ne = min(a.E, e_beg + a.chunk) - e_beg;
+  const int rows = ne * nb;
   const long N = a.N;
+  const unsigned expect = (unsigned)a.expect;
   unsigned nbar = 0;
 
   if (threadIdx.x == 0) sflag[1] = (*(volatile int*)a.status & ST_TIMEOUT) ? 1 : 0;
@@ -254,14 +274,14 @@ __global__ void __launch_bounds__(256) coop_smooth_kernel(CoopArgs<S> a) {
   if (sflag[1]) return;   // an earlier wait ran out: leave x as it is
 
   // r = b - A x into w, ||r||^2
-  bsr_own<S>(a, a.x, a.w, a.b, e_beg, e_end, xs, pt);
+  bsr_own<S>(a, a.x, a.b, ws, e_beg, ne, xs);
   {
     double s = 0.0;
-    for (long n = n0 + threadIdx.x; n < n1; n += blockDim.x) s += (double)a.w[n] * (double)a.w[n];
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += (double)ws[r] * (double)ws[r];
     s = block_sum(s, red);
     if (threadIdx.x == 0) mypart[2 * ldh] = s;
   }
-  if (!grid_barrier(a.bar, ++nbar * a.expect, a.status, sflag)) return;
+  if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
   sum_parts(1, a.part + 2 * ldh, stride, G, h2);
   const double beta = sqrt(h2[0]);
   if (!(beta > 0.0) || !isfinite(beta)) {
@@ -276,40 +296,40 @@ __global__ void __launch_bounds__(256) coop_smooth_kernel(CoopArgs<S> a) {
   int kdone = 0;
   for (int j = 0; j < nu; ++j) {
     // A: v_j = w / ||w||, z_j = D^{-1} v_j
-    float* vj = a.V + (size_t)j * N;
-    float* zj = a.Z + (size_t)j * N;
-    for (long n = n0 + threadIdx.x; n < n1; n += blockDim.x) vj[n] = (float)(inv * (double)a.w[n]);
+    float* vj = Vs + (size_t)j * rmax;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) vj[r] = (float)(inv * (double)ws[r]);
     __syncthreads();
-    bj_own<S>(a, vj, zj, e_beg, e_end, xs);
-    if (!grid_barrier(a.bar, ++nbar * a.expect, a.status, sflag)) return;
+    float* zg = a.Z + (size_t)j * N;
+    bj_own<S>(a, vj, Zs + (size_t)j * rmax, zg, e_beg, ne);
+    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
     // B: w = A z_j, first pass of inner products
-    bsr_own<S>(a, zj, a.w, nullptr, e_beg, e_end, xs, pt);
-    own_dots(j + 1, a.V, N, a.w, n0, n1, mypart);
-    if (!grid_barrier(a.bar, ++nbar * a.expect, a.status, sflag)) return;
+    bsr_own<S>(a, zg, nullptr, ws, e_beg, ne, xs);
+    own_dots(j + 1, Vs, rmax, ws, rows, mypart);
+    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
     // C: w -= V h1, second pass
     sum_parts(j + 1, a.part, stride, G, h1);
-    for (long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-      double acc = (double)a.w[n];
-      for (int i = 0; i <= j; ++i) acc -= h1[i] * (double)a.V[(size_t)i * N + n];
-      a.w[n] = (float)acc;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      double acc = (double)ws[r];
+      for (int i = 0; i <= j; ++i) acc -= h1[i] * (double)Vs[(size_t)i * rmax + r];
+      ws[r] = (float)acc;
     }
     __syncthreads();
-    own_dots(j + 1, a.V, N, a.w, n0, n1, mypart + ldh);
-    if (!grid_barrier(a.bar, ++nbar * a.expect, a.status, sflag)) return;
+    own_dots(j + 1, Vs, rmax, ws, rows, mypart + ldh);
+    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
     // D: w -= V h2, ||w||^2
     sum_parts(j + 1, a.part + ldh, stride, G, h2);
     double s = 0.0;
-    for (long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-      double acc = (double)a.w[n];
-      for (int i = 0; i <= j; ++i) acc -= h2[i] * (double)a.V[(size_t)i * N + n];
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      double acc = (double)ws[r];
+      for (int i = 0; i <= j; ++i) acc -= h2[i] * (double)Vs[(size_t)i * rmax + r];
       const float wf = (float)acc;
-      a.w[n] = wf;
+      ws[r] = wf;
       s += (double)wf * (double)wf;
     }
     s = block_sum(s, red);
     if (threadIdx.x == 0) mypart[2 * ldh] = s;
-    if (!grid_barrier(a.bar, ++nbar * a.expect, a.status, sflag)) return;
-    sum_parts(1, a.part + 2 * ldh, stride, G, red + 16);   // red[16] = ||w||^2 (red[0..7] free here)
+    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
+    sum_parts(1, a.part + 2 * ldh, stride, G, red + 16);   // red[16] = ||w||^2 (red[0..15] free here)
     const double hn = sqrt(red[16]);
     // Hessenberg column j, earlier rotations, new rotation, g (every CTA alike)
     if (threadIdx.x == 0) {
@@ -353,41 +373,50 @@ __global__ void __launch_bounds__(256) coop_smooth_kernel(CoopArgs<S> a) {
     }
   }
   __syncthreads();
-  for (long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-    double acc = (double)a.x[n];
-    for (int i = 0; i < kdone; ++i) acc += h1[i] * (double)a.Z[(size_t)i * N + n];
-    a.x[n] = (float)acc;
+  float* xo = a.x + (size_t)e_beg * nb;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+    double acc = (double)xo[r];
+    for (int i = 0; i < kdone; ++i) acc += h1[i] * (double)Zs[(size_t)i * rmax + r];
+    xo[r] = (float)acc;
   }
 }
 
-static size_t coop_smem(int nu, int nb, int ld, int nf, int epc, int tpe) {
+static size_t coop_smem(int nu, int nb, int nf, int chunk, int epc) {
   const size_t ldh = nu + 1;
   const size_t dbl = ldh * nu + 2 * (size_t)nu + 3 * ldh + 32;
-  const size_t xs = std::max((size_t)epc * (1 + nf) * nb, (size_t)(256 / tpe) * nb);
-  return dbl * sizeof(double) + 4 * sizeof(int) + (xs + (size_t)epc * (1 + nf) * ld) * sizeof(float);
+  const size_t rmax = (size_t)chunk * nb;
+  const size_t flt = (2 * (size_t)nu + 2) * rmax + (size_t)epc * (1 + nf) * nb;
+  return dbl * sizeof(double) + 4 * sizeof(int) + flt * sizeof(float);
 }
 
 template <class S>
 static cudaError_t plan_coop(int nb, int ld, int nf, int E, int nu, CoopPlan* plan) {
   constexpr int R = Col16<S>::R;
   plan->ok = 0;
-  if (ld % R) return cudaSuccess;
-  const int tpe = ld / R, tpb = (1 + nf) * tpe;
-  if (tpb > 256 || tpe > 256) return cudaSuccess;
-  const int epc = std::max(1, 256 / tpb);
-  const size_t smem = coop_smem(nu, nb, ld, nf, epc, tpe);
+  if (ld % R || E < 1) return cudaSuccess;
+  const int tpe = ld / R;
+  if (tpe > COOP_THREADS) return cudaSuccess;
   auto kern = coop_smooth_kernel<S>;
   cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
-  int occ = 0, dev = 0, nsm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem);
-  if (e != cudaSuccess) return e;
+  int dev = 0, nsm = 0, smax = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (occ < 1 || nsm < 1) return cudaSuccess;
-  int grid = std::min(E, std::min(occ, 2) * nsm);
+  cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (nsm < 1) return cudaSuccess;
+  int grid = std::min(E, nsm);
   const int chunk = (E + grid - 1) / grid;
   grid = (E + chunk - 1) / chunk;   // no CTA without elements
+  const int epc = std::max(1, std::min(chunk, COOP_THREADS / tpe));
+  const size_t smem = coop_smem(nu, nb, nf, chunk, epc);
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  if (smem + fa.sharedSizeBytes > (size_t)smax) return cudaSuccess;   // the rows do not fit: per-operation smoother
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, COOP_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaSuccess;
   plan->ok = 1;
   plan->nu_max = nu;
   plan->grid = grid;
@@ -414,9 +443,7 @@ static cudaError_t launch_coop(const CoopPlan& pl, const S* Dinv, const S* Dop, 
   a.nbr = nbr;
   a.b = b;
   a.x = x;
-  a.V = K.V;
   a.Z = K.Z;
-  a.w = K.w;
   a.part = part;
   a.bar = bar;
   a.status = status;
@@ -431,11 +458,11 @@ static cudaError_t launch_coop(const CoopPlan& pl, const S* Dinv, const S* Dop, 
   a.epc = pl.epc;
   a.tpe = pl.tpe;
   a.expect = pl.grid + expect_extra;
-  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(bar, 0, COOP_BAR_WORDS * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(pl.grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(COOP_THREADS);
   cfg.dynamicSmemBytes = pl.smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
