@@ -581,57 +581,74 @@ def batched_sample(B, count=64, workers=8, budget=120 << 30):
                       "submitted at once; wall time includes per-case mesh and preconditioner setup"}
 
 
-def serving_sample(B, count=16, max_dofs=300000, workers=4, budget=40 << 30, load=1.0, seed=1812):
-    """Serving workload, bounded sample: `count` requests of the serving mix
-    (2-D vortex 32^2-256^2 / 3-D TGV 8^3-32^3, p 1..6, FP64 or mixed), redrawn
-    above max_dofs.  Pass 1 runs the list at full concurrency (measures the
-    service rate, builds resident slots); pass 2 submits the same list with
-    Poisson arrivals at `load` x that rate.  Reports p50/p99 latency and DOFs/s."""
-    reqs = wl.serving_requests(count, seed=seed, max_dofs=max_dofs)
-    inputs = []
-    for cfg in reqs:
-        W0 = wl.initial_state(cfg)
-        dt = wl.time_step(cfg)
-        Wm1 = wl.initial_state(cfg, t=-dt) if cfg["case"] == "vortex" else W0.copy()
-        pl = cfg["p_levels"]
-        opts = B.pmg_opts(pl, nu_pre=10, nu_post=10, nu_coarse=30,
-                          cycle=B.CYCLE_FMG if len(pl) > 1 else B.CYCLE_BJ,
-                          precision=B.PREC_MIXED if cfg["mixed"] else B.PREC_FP64)
-        inputs.append((cfg, opts, W0, Wm1, dt, np.zeros_like(W0)))
+def serving_sample(B, count=40, max_dofs=1500000, workers=4, budget=80 << 30, loads=(0.25, 0.5, 1.0, 2.0, 4.0),
+                   seed=1812):
+    """Serving workload (the request mix of wl.serving_requests: 2-D vortex
+    32^2-256^2 / 3-D TGV 8^3-32^3, p 1..6, FP64 or mixed, one implicit step
+    each), redrawn above max_dofs so that the sweep ends in minutes: the
+    largest cases of the mix (up to 13.8 M DOFs; one FP64 step of TGV 32^3
+    p = 6 takes about 84 s) would hold the GPU for the whole run.  Pass 0 runs
+    one list at full concurrency (service rate, resident slots); then, for
+    every load factor, a fresh list of `count` requests arrives as a Poisson
+    stream at load x the service rate.  Reports p50/p99 latency (submit to
+    completion) and DOFs/s per load."""
+    def inputs_for(s):
+        out = []
+        for cfg in wl.serving_requests(count, seed=s, max_dofs=max_dofs):
+            W0 = wl.initial_state(cfg)
+            dt = wl.time_step(cfg)
+            Wm1 = wl.initial_state(cfg, t=-dt) if cfg["case"] == "vortex" else W0.copy()
+            pl = cfg["p_levels"]
+            opts = B.pmg_opts(pl, nu_pre=10, nu_post=10, nu_coarse=30,
+                              cycle=B.CYCLE_FMG if len(pl) > 1 else B.CYCLE_BJ,
+                              precision=B.PREC_MIXED if cfg["mixed"] else B.PREC_FP64)
+            out.append((cfg, opts, W0, Wm1, dt, np.zeros_like(W0)))
+        return out
+
     srv = B.Server(budget, workers)
+    sweep = []
     try:
+        first = inputs_for(seed)
         t0 = time.perf_counter()
-        for i, (cfg, opts, W0, Wm1, dt, out) in enumerate(inputs):
+        for i, (cfg, opts, W0, Wm1, dt, out) in enumerate(first):
             srv.submit(i, wl.mesh_desc(cfg), wl.physics(cfg), opts, W0, Wm1, dt, out)
         got = []
         while len(got) < count:
             got += srv.poll(1, timeout_ms=600000)
         rate = count / (time.perf_counter() - t0)
-        rng = np.random.default_rng(seed + 1)
-        gaps = rng.exponential(1.0 / (load * rate), count)
-        t0 = time.perf_counter()
-        due = t0
-        res = []
-        for i, (cfg, opts, W0, Wm1, dt, out) in enumerate(inputs):
-            due += gaps[i]
-            while time.perf_counter() < due:
-                res += srv.poll(0, timeout_ms=1)
-            srv.submit(1000 + i, wl.mesh_desc(cfg), wl.physics(cfg), opts, W0, Wm1, dt, out)
-        while len(res) < count:
-            res += srv.poll(1, timeout_ms=600000)
-        span = time.perf_counter() - t0
+        rid = 1000
+        for k, load in enumerate(loads):
+            reqs = inputs_for(seed + 1 + k)
+            rng = np.random.default_rng(seed + 100 + k)
+            gaps = rng.exponential(1.0 / (load * rate), count)
+            t0 = time.perf_counter()
+            due = t0
+            res = []
+            for i, (cfg, opts, W0, Wm1, dt, out) in enumerate(reqs):
+                due += gaps[i]
+                while time.perf_counter() < due:
+                    res += srv.poll(0, timeout_ms=1)
+                srv.submit(rid, wl.mesh_desc(cfg), wl.physics(cfg), opts, W0, Wm1, dt, out)
+                rid += 1
+            while len(res) < count:
+                res += srv.poll(1, timeout_ms=600000)
+            span = time.perf_counter() - t0
+            lat = sorted(r["latency_ms"] for r in res)
+            sweep.append({"load": load, "requests": count, "ok": int(sum(r["status"] == 0 for r in res)),
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "value": sum(c["dofs"] for c, *_ in reqs) / span, "unit": UNIT,
+                          "fgmres_iters_mean": float(np.mean([r["fgmres_iters"] for r in res]))})
         st = srv.stats()
     finally:
         srv.close()
-    lat = sorted(r["latency_ms"] for r in res)
-    ok = sum(r["status"] == 0 for r in res)
-    dofs = sum(c["dofs"] for c, *_ in inputs)
-    return {"requests": count, "ok": ok, "workers": workers, "load": load,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "value": dofs / span, "unit": UNIT, "service_rate_req_s": rate,
-            "resident_slots": st["resident_slots"], "budget_bytes": budget,
-            "sample": "serving mix (2-D vortex 32^2-256^2 / 3-D TGV 8^3-32^3, p 1..6, FP64|mixed), "
-                      "draws above %d DOFs redrawn; Poisson arrivals" % max_dofs}
+    one = next(x for x in sweep if x["load"] == 1.0)
+    return {"requests": count, "ok": one["ok"], "workers": workers, "load": 1.0,
+            "p50_ms": one["p50_ms"], "p99_ms": one["p99_ms"], "value": one["value"], "unit": UNIT,
+            "service_rate_req_s": rate, "resident_slots": st["resident_slots"], "budget_bytes": budget,
+            "sweep": sweep,
+            "sample": "serving mix (2-D vortex 32^2-256^2 / 3-D TGV 8^3-32^3, p 1..6, FP64|mixed), draws above "
+                      "%d DOFs redrawn (time bound: the largest FP64 requests take minutes); Poisson arrivals at "
+                      "%s x the measured service rate, %d requests per load" % (max_dofs, list(loads), count)}
 
 
 def cpu_baseline_sample(cfg, newton, time_budget=40.0):

@@ -164,38 +164,45 @@ __device__ void sum_parts(int nv, const double* part, int stride, int G, double*
 
 // ws[own rows of e] = [b_e -] (D_e in_e + sum_s O_{e,s} in_nbr(e,s)) for the
 // CTA's ne elements from e_beg: a thread per (element, R rows) sums all the
-// element's blocks; the inputs are staged in shared memory, epc elements a pass.
-template <class S>
+// element's blocks, column by column with the 1 + NF blocks' loads of a column
+// in flight together (the coarse levels are latency-bound); the inputs are
+// staged in shared memory, epc elements a pass.
+template <class S, int NF>
 __device__ void bsr_own(const CoopArgs<S>& a, const float* in, const float* bsub, float* ws, int e_beg, int ne,
                         float* xs) {
-  constexpr int R = Col16<S>::R;
-  const int nb = a.nb, ld = a.ld, nf = a.nf, nsrc = 1 + nf, tpe = a.tpe, epc = a.epc;
+  constexpr int R = Col16<S>::R, NSRC = 1 + NF;
+  const int nb = a.nb, ld = a.ld, tpe = a.tpe, epc = a.epc;
   const size_t bs = (size_t)nb * ld;
   const int sub = threadIdx.x / tpe, tt = threadIdx.x - sub * tpe;
   for (int p0 = 0; p0 < ne; p0 += epc) {
     const int nl = min(epc, ne - p0);
-    for (int t = threadIdx.x; t < nl * nsrc * nb; t += blockDim.x) {
-      const int el = t / (nsrc * nb), q = t - el * nsrc * nb, who = q / nb, j = q - who * nb;
+    for (int t = threadIdx.x; t < nl * NSRC * nb; t += blockDim.x) {
+      const int el = t / (NSRC * nb), q = t - el * NSRC * nb, who = q / nb, j = q - who * nb;
       const int e = e_beg + p0 + el;
-      const int src = who == 0 ? e : a.nbr[(size_t)e * nf + who - 1];
+      const int src = who == 0 ? e : a.nbr[(size_t)e * NF + who - 1];
       xs[t] = __ldcg(in + (size_t)src * nb + j);
     }
     __syncthreads();
     if (sub < nl) {
       const int e = e_beg + p0 + sub;
+      const S* base[NSRC];
+      base[0] = a.Dop + (size_t)e * bs + R * tt;
+#pragma unroll
+      for (int b = 1; b < NSRC; ++b) base[b] = a.O + ((size_t)e * NF + b - 1) * bs + R * tt;
+      const float* xe = xs + (size_t)sub * NSRC * nb;
       float acc[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) acc[j] = 0.f;
-      for (int blk = 0; blk < nsrc; ++blk) {
-        const S* base = (blk == 0 ? a.Dop + (size_t)e * bs : a.O + ((size_t)e * nf + blk - 1) * bs) + R * tt;
-        const float* xb = xs + ((size_t)sub * nsrc + blk) * nb;
-#pragma unroll 8
-        for (int c = 0; c < nb; ++c) {
-          float v[R];
-          Col16<S>::load(base + (size_t)c * ld, v);
-          const float xv = xb[c];
+#pragma unroll 2
+      for (int c = 0; c < nb; ++c) {
+        float v[NSRC][R];
 #pragma unroll
-          for (int j = 0; j < R; ++j) acc[j] += v[j] * xv;
+        for (int b = 0; b < NSRC; ++b) Col16<S>::load(base[b] + (size_t)c * ld, v[b]);
+#pragma unroll
+        for (int b = 0; b < NSRC; ++b) {
+          const float xv = xe[(size_t)b * nb + c];
+#pragma unroll
+          for (int j = 0; j < R; ++j) acc[j] += v[b][j] * xv;
         }
       }
       const int r0 = (p0 + sub) * nb + R * tt;
@@ -224,7 +231,7 @@ __device__ void bj_own(const CoopArgs<S>& a, const float* vs, float* zs, float* 
       float acc[R];
 #pragma unroll
       for (int j = 0; j < R; ++j) acc[j] = 0.f;
-#pragma unroll 8
+#pragma unroll 16
       for (int c = 0; c < nb; ++c) {
         float m[R];
         Col16<S>::load(base + (size_t)c * ld, m);
@@ -243,7 +250,7 @@ __device__ void bj_own(const CoopArgs<S>& a, const float* vs, float* zs, float* 
   }
 }
 
-template <class S>
+template <class S, int NF>
 __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nu = a.nu, ldh = nu + 1, nb = a.nb;
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
   if (sflag[1]) return;   // an earlier wait ran out: leave x as it is
 
   // r = b - A x into w, ||r||^2
-  bsr_own<S>(a, a.x, a.b, ws, e_beg, ne, xs);
+  bsr_own<S, NF>(a, a.x, a.b, ws, e_beg, ne, xs);
   {
     double s = 0.0;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) s += (double)ws[r] * (double)ws[r];
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
     bj_own<S>(a, vj, Zs + (size_t)j * rmax, zg, e_beg, ne);
     if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
     // B: w = A z_j, first pass of inner products
-    bsr_own<S>(a, zg, nullptr, ws, e_beg, ne, xs);
+    bsr_own<S, NF>(a, zg, nullptr, ws, e_beg, ne, xs);
     own_dots(j + 1, Vs, rmax, ws, rows, mypart);
     if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
     // C: w -= V h1, second pass
@@ -389,14 +396,14 @@ static size_t coop_smem(int nu, int nb, int nf, int chunk, int epc) {
   return dbl * sizeof(double) + 4 * sizeof(int) + flt * sizeof(float);
 }
 
-template <class S>
+template <class S, int NF>
 static cudaError_t plan_coop(int nb, int ld, int nf, int E, int nu, CoopPlan* plan) {
   constexpr int R = Col16<S>::R;
   plan->ok = 0;
   if (ld % R || E < 1) return cudaSuccess;
   const int tpe = ld / R;
   if (tpe > COOP_THREADS) return cudaSuccess;
-  auto kern = coop_smooth_kernel<S>;
+  auto kern = coop_smooth_kernel<S, NF>;
   cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0, smax = 0;
@@ -428,8 +435,14 @@ static cudaError_t plan_coop(int nb, int ld, int nf, int E, int nu, CoopPlan* pl
 }
 
 cudaError_t plan_coop_smoother(int bf16, int nb, int nf, int E, int nu, CoopPlan* plan) {
-  return bf16 ? plan_coop<unsigned short>(nb, ld_bf16(nb), nf, E, nu, plan)
-              : plan_coop<float>(nb, inv_ld<float>(nb), nf, E, nu, plan);
+  plan->ok = 0;
+  if (nf == 6)
+    return bf16 ? plan_coop<unsigned short, 6>(nb, ld_bf16(nb), nf, E, nu, plan)
+                : plan_coop<float, 6>(nb, inv_ld<float>(nb), nf, E, nu, plan);
+  if (nf == 4)
+    return bf16 ? plan_coop<unsigned short, 4>(nb, ld_bf16(nb), nf, E, nu, plan)
+                : plan_coop<float, 4>(nb, inv_ld<float>(nb), nf, E, nu, plan);
+  return cudaSuccess;   // other face counts keep the launch-per-operation smoother
 }
 
 template <class S>
@@ -471,7 +484,8 @@ static cudaError_t launch_coop(const CoopPlan& pl, const S* Dinv, const S* Dop, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   note_launch();
-  return cudaLaunchKernelEx(&cfg, coop_smooth_kernel<S>, a);
+  if (nf == 6) return cudaLaunchKernelEx(&cfg, coop_smooth_kernel<S, 6>, a);
+  return cudaLaunchKernelEx(&cfg, coop_smooth_kernel<S, 4>, a);
 }
 
 cudaError_t launch_coop_smoother(const CoopPlan& pl, const float* Dinv, const float* Dop, const float* O,
