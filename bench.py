@@ -56,6 +56,13 @@ def parse():
     ap.add_argument("--no-large-dt", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--c3-fp64", type=int, default=1, help="FP64 steps of the 32^3 p=6 case (0: skip)")
+    # profiling mode: one library operation a few times (ncu launch lists and captures)
+    ap.add_argument("--profile-op", default=None,
+                    choices=["jvp64", "residual64", "bj", "apply", "refresh", "fgmres", "step"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--n", type=int, nargs="*", default=None, help="override the mesh size (--profile-op)")
+    ap.add_argument("--bf16", action="store_true", help="BF16 block storage (--profile-op)")
     return ap.parse_args()
 
 
@@ -581,7 +588,7 @@ def batched_sample(B, count=64, workers=8, budget=120 << 30):
                       "submitted at once; wall time includes per-case mesh and preconditioner setup"}
 
 
-def serving_sample(B, count=40, max_dofs=1500000, workers=4, budget=80 << 30, loads=(0.25, 0.5, 1.0, 2.0, 4.0),
+def serving_sample(B, count=32, max_dofs=1000000, workers=4, budget=80 << 30, loads=(0.25, 0.5, 1.0, 2.0, 4.0),
                    seed=1812):
     """Serving workload (the request mix of wl.serving_requests: 2-D vortex
     32^2-256^2 / 3-D TGV 8^3-32^3, p 1..6, FP64 or mixed, one implicit step
@@ -853,6 +860,79 @@ def run_gb300(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile_op(args):
+    """Run one library operation --reps times after --warmup untimed ones, for
+    profiling (ncu launch lists and kernel captures) and quick CUDA-event
+    timings: jvp64 (FP64 exact JVP), residual64, bj (block-Jacobi apply), apply
+    (one pMG application), refresh (preconditioner update), fgmres (one linear
+    solve), step (one BDF2 step with --newton Newton iterations).  Prints the
+    event milliseconds per repetition and the library's launches per repetition."""
+    import torch
+    from paper_1812_04789_gb300 import binding as B
+    from paper_1812_04789_gb300 import build as BLD
+    BLD.build()
+    B.load()
+    cfg = dict(wl.CONFIGS[args.config])
+    if args.n:
+        cfg["n"] = tuple(args.n) + (1,) * (3 - len(args.n))
+    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    storage = B.STORE_BF16 if args.bf16 else B.STORE_NATIVE
+    st = torch.cuda.Stream()
+    op = args.profile_op
+    with torch.cuda.stream(st):
+        m = B.Mesh.from_workload(wl.mesh_desc(cfg), wl.physics(cfg), stream=st)
+        W = torch.from_numpy(wl.initial_state(cfg)).cuda()
+        dt = wl.time_step(cfg)
+        sigma = 1.5 / dt
+        v = torch.randn_like(W)
+        out = torch.empty_like(W)
+        pl = cfg["p_levels"]
+        o = B.pmg_opts(pl, 10, 10, 30, cycle=B.CYCLE_FMG if len(pl) > 1 else B.CYCLE_BJ, precision=prec,
+                       storage=storage)
+        pmg = B.PMG(m, W, sigma, o, stream=st) if op in ("apply", "refresh", "fgmres", "step") else None
+        bj = None
+        if op == "bj":
+            bj = B.PMG(m, W, sigma, B.pmg_opts((cfg["p"],), cycle=B.CYCLE_BJ, precision=prec, storage=storage),
+                       stream=st)
+        b = torch.empty_like(W)
+        m.bdf2_rhs(W, W, W, dt, b, stream=st)
+        Wk = torch.empty_like(W)
+
+        def run():
+            if op == "jvp64":
+                m.jvp(W, v, out, sigma, stream=st)
+            elif op == "residual64":
+                m.residual(W, out, stream=st)
+            elif op == "bj":
+                bj.apply(v, out, stream=st)
+            elif op == "apply":
+                pmg.apply(v, out, stream=st)
+            elif op == "refresh":
+                pmg.refresh(W, sigma, stream=st)
+            elif op == "fgmres":
+                pmg.fgmres(W, b, out, stream=st)
+            else:
+                pmg.refresh(W, sigma, stream=st)
+                Wk.copy_(W)
+                for _ in range(args.newton):
+                    m.bdf2_rhs(Wk, W, W, dt, b, stream=st)
+                    pmg.fgmres(Wk, b, out, stream=st)
+                    m.axpy(1.0, out, Wk, stream=st)
+        for _ in range(args.warmup):
+            run()
+        torch.cuda.synchronize()
+        l0 = B.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.reps):
+            run()
+        e1.record(st)
+        e1.synchronize()
+        print(json.dumps({"op": op, "precision": args.precision, "config": args.config, "n": cfg["n"],
+                          "bf16": args.bf16, "ms_per_rep": e0.elapsed_time(e1) / args.reps,
+                          "launches_per_rep": (B.launch_count() - l0) / args.reps}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -880,7 +960,9 @@ def run_reference(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_op:
+        run_profile_op(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gb300(args)

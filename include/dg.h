@@ -256,6 +256,7 @@ typedef struct {
   double rho;           /* (res_final/res0)^(1/iters), Sec. 7.3 */
   int status;           /* dg_status of the solve */
   float ms_total;       /* device time of the call */
+  float ms_setup;       /* host time spent building the cycle graph in this call (0 when reused) */
 } dg_krylov_stats;
 
 /* Solve K dW = b (eq. ODEDG: the caller passes b = -f of the Newton step,
@@ -263,8 +264,14 @@ typedef struct {
  * preconditioned by pmg (setup at the same mesh; its sigma must be the one
  * given here), Arnoldi by classical Gram-Schmidt applied twice, Givens
  * rotations.  The outer Krylov vectors and the JVP are FP64.  W, b, dW: device
- * FP64.  Blocks until the solve ends (it reads the residual estimate once per
- * iteration); stats (host, may be NULL) is filled in.  Returns DG_OK,
+ * FP64.  With the exact JVP on a structured mesh the convergence test runs on
+ * the device: a restart cycle is one launch of a graph in which every
+ * iteration sits behind a conditional node that the previous iteration's test
+ * opens (built at the first call and again when restart or sigma changes; it
+ * works on copies of W and b in the handle, so a call may pass other pointers),
+ * and the host waits once per cycle; the FD modes and triangle meshes read the
+ * residual estimate on the host once per iteration.  Blocks until the solve
+ * ends; stats (host, may be NULL) is filled in.  Returns DG_OK,
  * DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN or an error of the calls above. */
 dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, const double* b,
                          double sigma, const dg_krylov_opts* opts, double* dW,

@@ -71,7 +71,8 @@ class KrylovOpts(ctypes.Structure):
 
 class KrylovStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("res0", ctypes.c_double), ("res_final", ctypes.c_double),
-                ("rho", ctypes.c_double), ("status", ctypes.c_int), ("ms_total", ctypes.c_float)]
+                ("rho", ctypes.c_double), ("status", ctypes.c_int), ("ms_total", ctypes.c_float),
+                ("ms_setup", ctypes.c_float)]
 
 
 _lib = None
@@ -383,7 +384,7 @@ class PMG:
                                      float(self.sigma if sigma is None else sigma), ctypes.byref(ko),
                                      _ptr(dW), ctypes.byref(st), _stream(stream))
         out = dict(iters=st.iters, res0=st.res0, res_final=st.res_final, rho=st.rho, status=code,
-                   ms_total=st.ms_total)
+                   ms_total=st.ms_total, ms_setup=st.ms_setup)
         if raise_on_error and code != DG_OK:
             raise DGError("dg_fgmres_step", code)
         return out

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <type_traits>
 
 #include "dg_internal.h"
@@ -163,15 +164,17 @@ cudaError_t MG<T>::apply(const T* r, T* z, cudaStream_t st) {
   const long nev = (long)mesh->E * mesh->m;
   if (cycle == DG_CYCLE_BJ)
     return bj_apply<T>(lv[0], r, z, mesh->E, st);
+  // (copies by kernel: the application is also captured into conditional graph
+  // bodies, where kernels and memsets are the node types used)
   if (cycle == DG_CYCLE_V) {
-    CKE(cudaMemcpyAsync(lv[0].b, r, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st));
+    CKE(launch_axpby<T>(lv[0].N, 1.0, r, 0.0, lv[0].b, st));
     CKE(cudaMemsetAsync(lv[0].x, 0, sizeof(T) * lv[0].N, st));
     CKE(mg_v(0, st));
-    return cudaMemcpyAsync(z, lv[0].x, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st);
+    return launch_axpby<T>(lv[0].N, 1.0, lv[0].x, 0.0, z, st);
   }
   // MG_full (Algorithm 1): b_l = I_0^l b_0 on every level, SOLVE on the
   // coarsest, then for l = L-1..0: x~_l = I_{l+1}^l x_{l+1}, x_l = MG_V(l, b_l, x~_l)
-  CKE(cudaMemcpyAsync(lv[0].b, r, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st));
+  CKE(launch_axpby<T>(lv[0].N, 1.0, r, 0.0, lv[0].b, st));
   for (int l = 1; l <= Lc; ++l) CKE(launch_restrict<T>(r, lv[0].nm, lv[l].b, lv[l].nm, nev, st));
   CKE(cudaMemsetAsync(lv[Lc].x, 0, sizeof(T) * lv[Lc].N, st));
   CKE(smooth(Lc, lv[Lc].b, lv[Lc].x, nu_coarse, st));
@@ -179,7 +182,7 @@ cudaError_t MG<T>::apply(const T* r, T* z, cudaStream_t st) {
     CKE(launch_prolong<T>(lv[l + 1].x, lv[l + 1].nm, lv[l].x, lv[l].nm, nev, false, st));
     CKE(mg_v(l, st));
   }
-  return cudaMemcpyAsync(z, lv[0].x, sizeof(T) * lv[0].N, cudaMemcpyDeviceToDevice, st);
+  return launch_axpby<T>(lv[0].N, 1.0, lv[0].x, 0.0, z, st);
 }
 
 template struct MG<double>;
@@ -488,6 +491,8 @@ static dg_status check_opts(const dg_mesh_s* mesh, const dg_pmg_opts* o) {
 
 extern "C" dg_status dg_pmg_destroy(dg_pmg h) {
   if (!h) return DG_ERR_INVALID;
+  if (h->fgm_exec) cudaGraphExecDestroy(h->fgm_exec);
+  if (h->fgm_graph) cudaGraphDestroy(h->fgm_graph);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -749,6 +754,266 @@ extern "C" dg_status dg_pmg_export_blocks(dg_pmg h, int level, int which, void* 
   return export_level<float>(h->mg32, M, h->mg32.W, h->sigma, level, which, (float*)out, out_bytes, st);
 }
 
+// ---------------------------------------------------------------- device-driven FGMRES cycle
+namespace dgk {
+// prm: [0] rtol, [1] atol, [2] ||b|| (set on cycle 0), [3] tol, [4] residual estimate, [5] cycle
+// iq:  [0] iterations of this cycle, [1] stop reason (0 none yet, 1 converged, 2 non-finite,
+//      3 iteration limit, 4 Krylov space exhausted)
+__global__ void fgm_start_kernel(cudaGraphConditionalHandle h0, const double* res, int* kdim, double* prm, int* iq) {
+  const double beta = res[1];
+  if (prm[5] == 0.0) prm[2] = beta;
+  const double tol = fmax(prm[0] * prm[2], prm[1]);
+  prm[3] = tol;
+  prm[4] = beta;
+  iq[0] = 0;
+  iq[1] = 0;
+  const bool fin = isfinite(beta) != 0;
+  const bool go = fin && beta > tol;
+  if (!go) {
+    kdim[0] = 0;
+    iq[1] = fin ? 1 : 2;
+  }
+  cudaGraphSetConditional(h0, go ? 1u : 0u);
+}
+
+__global__ void fgm_check_kernel(cudaGraphConditionalHandle hn, int has_next, int j, int restart, const double* res,
+                                 int* kdim, double* prm, int* iq) {
+  const double r = res[0];
+  prm[4] = r;
+  iq[0] = j + 1;
+  const bool nonfin = (kdim[1] & ST_NONFINITE) || !isfinite(r);
+  const bool conv = !nonfin && r <= prm[3];
+  const bool exhausted = kdim[0] <= j + 1 && j + 1 < restart;
+  const bool stop = conv || nonfin || exhausted || j + 1 >= restart;
+  if (stop) {
+    if (kdim[0] > j + 1) kdim[0] = j + 1;
+    iq[1] = conv ? 1 : (nonfin ? 2 : (exhausted ? 4 : 3));
+  }
+  if (has_next) cudaGraphSetConditional(hn, stop ? 0u : 1u);
+}
+}  // namespace dgk
+
+// Last node of a graph (the node nothing depends on).
+static cudaError_t last_node(cudaGraph_t g, cudaGraphNode_t* out) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess || n == 0) return e != cudaSuccess ? e : cudaErrorInvalidValue;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if ((e = cudaGraphGetNodes(g, nodes.data(), &n)) != cudaSuccess) return e;
+  for (size_t i = 0; i < n; ++i) {
+    size_t nd = 0;
+    if ((e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nd)) != cudaSuccess) return e;
+    if (nd == 0) {
+      *out = nodes[i];
+      return cudaSuccess;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// One FGMRES iteration's work on the handle's capture stream (captured, not run):
+// z_j = P^{-1} v_j (the preconditioner application), w = K z_j (exact FP64
+// JVP at fgm_W), CGS2 + Givens.
+static cudaError_t fgm_iteration(dg_pmg h, int j, cudaStream_t st) {
+  const Mesh& M = h->mesh->m;
+  const long N0 = (long)M.E * M.nb;
+  Krylov<double>& K = h->outer;
+  if (h->precision == DG_PREC_FP64) {
+    CKE(h->mg64.apply(K.Vj(j), K.Zj(j), st));
+  } else {
+    CKE(launch_convert<double, float>(N0, K.Vj(j), h->r32, st));
+    CKE(h->mg32.apply(h->r32, h->z32, st));
+    CKE(launch_convert<float, double>(N0, h->z32, K.Zj(j), st));
+  }
+  CKE(launch_residual<double>(M, h->fgm_W, K.Zj(j), nullptr, h->fgm_sigma, true, K.w, st));
+  return K.arnoldi(j, st);
+}
+
+// Build the cycle graph for `restart` iterations at shift sigma.
+static cudaError_t build_fgm_graph(dg_pmg h, int restart, double sigma) {
+  const long N0 = (long)h->mesh->m.E * h->mesh->m.nb;
+  if (!h->fgm_W) {
+    CKE(dalloc(h->allocs, (void**)&h->fgm_W, sizeof(double) * N0, &h->vector_bytes));
+    CKE(dalloc(h->allocs, (void**)&h->fgm_r0, sizeof(double) * N0, &h->vector_bytes));
+    CKE(dalloc(h->allocs, (void**)&h->fgm_dW, sizeof(double) * N0, &h->vector_bytes));
+    CKE(dalloc(h->allocs, (void**)&h->fgm_prm, sizeof(double) * 8, &h->vector_bytes));
+    CKE(dalloc(h->allocs, (void**)&h->fgm_iq, sizeof(int) * 4, &h->vector_bytes));
+  }
+  if (!h->cap_stream) CKE(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (h->fgm_exec) cudaGraphExecDestroy(h->fgm_exec);
+  if (h->fgm_graph) cudaGraphDestroy(h->fgm_graph);
+  h->fgm_exec = nullptr;
+  h->fgm_graph = nullptr;
+  h->fgm_sigma = sigma;
+  h->fgm_restart = restart;
+  cudaStream_t st = h->cap_stream;
+  Krylov<double>& K = h->outer;
+  cudaGraph_t g = nullptr;
+  CKE(cudaGraphCreate(&g, 0));
+  std::vector<cudaGraphConditionalHandle> hc(restart);
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < restart && e == cudaSuccess; ++j)
+    e = cudaGraphConditionalHandleCreate(&hc[j], g, 0, cudaGraphCondAssignDefault);
+  auto counter = [] { return __atomic_load_n(&launch_counter(), __ATOMIC_RELAXED); };
+  const unsigned long long l0 = counter();
+  // head: v_0 = r0 / ||r0||, g = (||r0||, 0, ...), tolerance, open iteration 0
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = K.start(h->fgm_r0, st);
+    if (e1 == cudaSuccess) {
+      note_launch();
+      fgm_start_kernel<<<1, 1, 0, st>>>(hc[0], K.res, K.kdim, h->fgm_prm, h->fgm_iq);
+      e1 = cudaGetLastError();
+    }
+    cudaGraph_t gg = g;
+    e = cudaStreamEndCapture(st, &gg);
+    if (e == cudaSuccess) e = e1;
+  }
+  const unsigned long long l1 = counter();
+  unsigned long long lb = 0;
+  for (int j = 0; j < restart && e == cudaSuccess; ++j) {
+    cudaGraphNode_t prev;
+    if ((e = last_node(g, &prev)) != cudaSuccess) break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc[j];
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, &prev, nullptr, 1, &cp)) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const unsigned long long b0 = counter();
+    if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
+      break;
+    cudaError_t e1 = fgm_iteration(h, j, st);
+    if (e1 == cudaSuccess) {
+      note_launch();
+      fgm_check_kernel<<<1, 1, 0, st>>>(j + 1 < restart ? hc[j + 1] : hc[j], j + 1 < restart ? 1 : 0, j, restart,
+                                        K.res, K.kdim, h->fgm_prm, h->fgm_iq);
+      e1 = cudaGetLastError();
+    }
+    cudaGraph_t bb = body;
+    e = cudaStreamEndCapture(st, &bb);
+    if (e == cudaSuccess) e = e1;
+    lb = std::max(lb, counter() - b0);
+  }
+  const unsigned long long l2 = counter();
+  // tail: dW += Z y over the effective Krylov dimension
+  if (e == cudaSuccess) {
+    cudaGraphNode_t prev;
+    e = last_node(g, &prev);
+    if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(st, g, &prev, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = K.update(restart, h->fgm_dW, st);
+      cudaGraph_t gg = g;
+      e = cudaStreamEndCapture(st, &gg);
+      if (e == cudaSuccess) e = e1;
+    }
+  }
+  const unsigned long long l3 = counter();
+  __atomic_fetch_sub(&launch_counter(), l3 - l0, __ATOMIC_RELAXED);   // captured, not run
+  h->fgm_head_k = l1 - l0;
+  h->fgm_body_k = lb;
+  h->fgm_tail_k = l3 - l2;
+  (void)l2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->fgm_exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (h->fgm_exec) cudaGraphExecDestroy(h->fgm_exec);
+    cudaGraphDestroy(g);
+    h->fgm_exec = nullptr;
+    return e;
+  }
+  h->fgm_graph = g;
+  return cudaSuccess;
+}
+
+// FGMRES with the exact JVP through the cycle graph: one host synchronisation
+// per restart cycle.  Returns DG_ERR_UNSUPPORTED when the graph is not
+// available (the caller then runs the host-driven loop).
+static dg_status fgmres_graph(dg_pmg h, const double* W, const double* b, double sigma, const dg_krylov_opts* ko,
+                              int restart, double* dW, dg_krylov_stats* stats, cudaStream_t st) {
+  const char* env = getenv("DG_FGMRES_HOST");
+  if (h->fgm_state < 0 || (env && env[0] == '1')) return DG_ERR_UNSUPPORTED;
+  float ms_setup = 0.f;
+  if (h->fgm_state == 0 || h->fgm_restart != restart || h->fgm_sigma != sigma) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (build_fgm_graph(h, restart, sigma) != cudaSuccess) {
+      h->fgm_state = -1;
+      return DG_ERR_UNSUPPORTED;
+    }
+    h->fgm_state = 1;
+    ms_setup = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  const Mesh& M = h->mesh->m;
+  const long N = (long)M.E * M.nb;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  CK(cudaMemcpyAsync(h->fgm_W, W, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(h->fgm_r0, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(h->fgm_dW, 0, sizeof(double) * N, st));
+  double prm[8] = {ko->rtol, ko->atol, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  dg_status s = DG_OK;
+  int iters = 0;
+  double bnorm = 0.0, res = 0.0;
+  bool converged = false;
+  for (int cycle = 0; cycle <= ko->max_restarts; ++cycle) {
+    prm[5] = (double)cycle;
+    if (cycle > 0) {   // restart from the true residual b - K dW
+      CK(launch_residual<double>(M, h->fgm_W, h->fgm_dW, nullptr, sigma, true, h->fgm_r0, st));
+      CK(launch_axpby<double>(N, 1.0, b, -1.0, h->fgm_r0, st));
+    }
+    // the cycle's parameters (rtol, atol; ||b|| is kept from cycle 0)
+    CK(cudaMemcpyAsync(h->fgm_prm, prm, sizeof(double) * 2, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->fgm_prm + 5, prm + 5, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaGraphLaunch(h->fgm_exec, st));
+    double hp[8];
+    int hq[4];
+    CK(cudaMemcpyAsync(hp, h->fgm_prm, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hq, h->fgm_iq, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    __atomic_fetch_add(&launch_counter(), h->fgm_head_k + h->fgm_tail_k + (unsigned long long)hq[0] * h->fgm_body_k,
+                       __ATOMIC_RELAXED);
+    iters += hq[0];
+    if (cycle == 0) bnorm = hp[2];
+    res = hp[4];
+    if (hq[1] == 2) {
+      s = DG_ERR_BREAKDOWN;
+      break;
+    }
+    if (hq[1] == 1 || hq[1] == 4) {
+      converged = hq[1] == 1 || res <= hp[3];
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(dW, h->fgm_dW, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  cudaEventRecord(e1, st);
+  float ms = 0.f;
+  if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == DG_OK && !converged) s = DG_ERR_NOT_CONVERGED;
+  if (s == DG_OK) {
+    int hs = 0;
+    cudaMemcpy(&hs, M.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (hs & ST_TIMEOUT) s = DG_ERR_TIMEOUT;
+    else if (hs & ST_NONPHYSICAL) s = DG_ERR_NONPHYSICAL;
+  }
+  if (stats) {
+    stats->iters = iters;
+    stats->res0 = bnorm;
+    stats->res_final = res;
+    stats->rho = (iters > 0 && bnorm > 0) ? pow(res / bnorm, 1.0 / iters) : 0.0;
+    stats->status = s;
+    stats->ms_total = ms;
+    stats->ms_setup = ms_setup;
+  }
+  return s;
+}
+
 extern "C" dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, const double* b, double sigma,
                                     const dg_krylov_opts* kopts, double* dW, dg_krylov_stats* stats,
                                     void* stream) {
@@ -760,6 +1025,12 @@ extern "C" dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, c
   const int mode = kopts->jvp_mode;
   if (mode != DG_JVP_EXACT && mode != DG_JVP_FD && mode != DG_JVP_FD_SCALED) return DG_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)stream;
+  if (mode == DG_JVP_EXACT && pmg->mesh->m.kind == DG_MESH_STRUCTURED) {
+    // device-driven cycles: the convergence test runs on the device, the host
+    // waits once per restart cycle
+    dg_status gs = fgmres_graph(pmg, W, b, sigma, kopts, restart, dW, stats, st);
+    if (gs != DG_ERR_UNSUPPORTED) return gs;
+  }
   const Mesh& M = mesh->m;
   const long N = (long)M.E * M.nb;
   Krylov<double>& K = pmg->outer;
@@ -838,6 +1109,7 @@ extern "C" dg_status dg_fgmres_step(dg_mesh mesh, dg_pmg pmg, const double* W, c
     stats->rho = (iters > 0 && bnorm > 0) ? pow(res / bnorm, 1.0 / iters) : 0.0;
     stats->status = s;
     stats->ms_total = ms;
+    stats->ms_setup = 0.f;
   }
   return s;
 }

@@ -390,6 +390,21 @@ struct dg_pmg_s {
   cudaGraphExec_t graph_exec = nullptr;
   unsigned long long graph_kernels = 0;
   double graph_sigma = 0;    // the shift the graph was captured with (a by-value kernel argument)
+  // one FGMRES cycle (exact JVP) as a graph: the head, `restart` iterations
+  // each behind a conditional (IF) node that the previous iteration's
+  // convergence check opens or leaves shut, and the solution update; it works
+  // on staging vectors so the caller's pointers can change between solves
+  cudaGraph_t fgm_graph = nullptr;
+  cudaGraphExec_t fgm_exec = nullptr;
+  int fgm_state = 0;          // 0: not built, 1: ready, -1: not available (host-driven loop)
+  int fgm_restart = 0;
+  double fgm_sigma = 0;
+  double* fgm_W = nullptr;    // the linearisation state
+  double* fgm_r0 = nullptr;   // the cycle's starting residual (b, or b - K dW after a restart)
+  double* fgm_dW = nullptr;   // the solution, accumulated over cycles
+  double* fgm_prm = nullptr;  // device scalars: rtol, atol, ||b||, tol, residual estimate, cycle
+  int* fgm_iq = nullptr;      // device ints: iterations of the cycle, stop reason
+  unsigned long long fgm_head_k = 0, fgm_body_k = 0, fgm_tail_k = 0;   // kernels per part (launch accounting)
   std::vector<void*> allocs;
   size_t block_bytes = 0, vector_bytes = 0;
 };

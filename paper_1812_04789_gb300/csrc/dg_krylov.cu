@@ -229,9 +229,12 @@ __global__ void lsq_kernel(const double* H, int ld, const double* g, int kdone, 
   }
 }
 
+// x += Z y over the first min(k, *kdim) directions (the directions past the
+// effective Krylov dimension may hold anything: they are not read)
 template <class T>
 __global__ void update_kernel(const T* __restrict__ Z, long N, const double* __restrict__ y, int k,
-                              T* __restrict__ x) {
+                              const int* __restrict__ kdim, T* __restrict__ x) {
+  k = min(k, *kdim);
   for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
     double acc = (double)x[n];
     for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * N + n];
@@ -334,7 +337,7 @@ cudaError_t Krylov<T>::update(int kdone, T* x, cudaStream_t st) {
   note_launch();
   lsq_kernel<<<1, 32, 0, st>>>(H, nmax + 1, g, kdone, kdim, y, nmax);
   note_launch();
-  update_kernel<T><<<grid_for(N), 256, 0, st>>>(Z, N, y, kdone, x);
+  update_kernel<T><<<grid_for(N), 256, 0, st>>>(Z, N, y, kdone, kdim, x);
   return cudaGetLastError();
 }
 
