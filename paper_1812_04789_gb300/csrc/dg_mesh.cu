@@ -350,7 +350,7 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
     return err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
   if ((err = upload_tables<float>(M, M.t32, tabs)) != cudaSuccess)
     return err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
-  if (desc->space == DG_SPACE_Q) {   // one-dimensional factors for sum factorisation
+  {   // one-dimensional factors for sum factorisation (Q_p, and P_p embedded in Q_p)
     const int n1 = p + 1;
     std::vector<double> l1d((size_t)2 * n1 * nq1 + nq1);
     for (int a = 0; a < n1; ++a)

@@ -17,6 +17,7 @@
 // With S = Dual<T> the same code carries the directional derivative: the JVP
 // is the exact linearisation of the discrete residual.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "dg_internal.h"
@@ -491,7 +492,16 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
     if (e != cudaSuccess) return e;
   }
   if (!(parts & 2)) return cudaSuccess;
-  if (Ms.desc.space == DG_SPACE_Q) {   // sum factorisation when it fits
+  // volume term by sum factorisation (Q_p; P_p embedded in Q_p, 3-D) when its
+  // stages fit shared memory, except in FP32 where the shared-memory kernel's
+  // tables fit (it reads the cached primal traces and interpolates only the
+  // direction); DG_NO_SUMFACT_P=1 keeps the direct kernels for P_p
+  size_t tsm0 = 0;
+  int nqp0 = 0;
+  const bool st_fits = std::is_same<T, float>::value && vol_tables_fit(Ms, JVP, &tsm0, &nqp0);
+  const char* nsf = getenv("DG_NO_SUMFACT_P");
+  const bool sumfact = Ms.desc.space == DG_SPACE_Q || (!(nsf && nsf[0] == '1') && !st_fits && Ms.d == 3);
+  if (sumfact) {
     cudaError_t eq = launch_volume_q<T>(Ms, W, V, S, sigma, JVP, out, st);
     if (eq != cudaErrorNotSupported) return eq;
     (void)cudaGetLastError();

@@ -8,6 +8,9 @@
 // contractions (the last one fused into the pointwise flux evaluation), and
 // the projection  R_i -= sum_q w_q grad phi_i(q) . F(q)  is the transposed
 // sequence: O((p+1) nq^d) work per contraction instead of O((p+1)^d nq^d).
+// The total-degree space P_p is the subset a0 + a1 + a2 <= p of the same
+// products, so its fields run through the same contractions with the other
+// tensor coefficients zero (qidx = -1) and only its modes are written back.
 // Interpolation (3-D): Z_s[v][a0][a1][q2] = sum_a2 W[v][a0 a1 a2] L^s_a2(q2)
 // (s = value or derivative factor), Y_t[v][a0][q1][q2] = sum_a1 Z L^t_a1(q1)
 // for the three patterns (L, L), (L', L)... needed by u, d/dxi_1, d/dxi_2,
@@ -85,8 +88,8 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
     for (int t = threadIdx.x; t < M * nt; t += blockDim.x) {
       const int v = t / nt, ti = t - v * nt, i = qidx[ti];
-      Wt[t] = W[(size_t)e * nb + v * mv.nm + i];
-      if (JVP) Wt[M * nt + t] = V[(size_t)e * nb + v * mv.nm + i];
+      Wt[t] = i >= 0 ? W[(size_t)e * nb + v * mv.nm + i] : T(0);
+      if (JVP) Wt[M * nt + t] = i >= 0 ? V[(size_t)e * nb + v * mv.nm + i] : T(0);
     }
     __syncthreads();
     // ---------------- interpolation
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
     // ---------------- modes: volume part + face slots (fixed order) + sigma |J| v or - source
     for (int t = threadIdx.x; t < M * nt; t += blockDim.x) {
       const int v = t / nt, ti = t - v * nt, i = qidx[ti], j = v * mv.nm + i;
+      if (i < 0) continue;   // a tensor coefficient outside P_p
       T acc = R[t];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -316,7 +320,7 @@ cudaError_t run_q(const Mesh& Ms, const T* W, const T* V, const T* S, T sigma, T
 template <class T>
 cudaError_t launch_volume_q(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
                             cudaStream_t st) {
-  if (M.desc.space != DG_SPACE_Q || !M.qidx) return cudaErrorNotSupported;
+  if (M.kind != DG_MESH_STRUCTURED || !M.qidx) return cudaErrorNotSupported;
   if (M.d == 2)
     return jvp ? run_q<2, T, true>(M, W, V, S, sigma, out, st) : run_q<2, T, false>(M, W, V, S, sigma, out, st);
   return jvp ? run_q<3, T, true>(M, W, V, S, sigma, out, st) : run_q<3, T, false>(M, W, V, S, sigma, out, st);
