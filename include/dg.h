@@ -137,9 +137,9 @@ dg_status dg_residual(dg_mesh mesh, const double* W, const double* S, double* R,
  * entry point).  Such callers include applications that reserve all device
  * memory at start-up and time-critical loops that must stay out of the CUDA
  * allocator.  Same arguments as dg_residual and the same result: the same
- * kernels on P_p meshes; on Q_p meshes the volume term takes the direct
- * contractions where dg_residual sums it by factorisation, so the two agree
- * to rounding there.  The face-slot scratch is a fixed file-scope device
+ * face kernel, while the volume term takes the direct contractions where
+ * dg_residual sums it by factorisation (3-D meshes and Q_p meshes), so the
+ * two agree to rounding there and bit for bit elsewhere.  The face-slot scratch is a fixed file-scope device
  * array of 2^20 doubles (8 MiB) that every GPU loading the library holds
  * until the process exits, instead of the mesh handle's workspace.
  * Limits: E * dim * 2 * m * n_m must not exceed 2^20, else DG_ERR_INVALID.

@@ -22,8 +22,10 @@
 // per thread plus two shared-memory vectors (the pivot row and column) and
 // three barriers.  The permuted, transposed result is staged in shared memory
 // and written out coalesced.
-// block_inverse_kernel (larger blocks): the block in shared memory (or global
-// memory when it does not fit), one warp per row in the update.
+// block_inverse_kernel (larger blocks): the block in shared memory, one warp
+// per row in the update.  block_inverse_panel_kernel (blocks that do not fit
+// shared memory): panels of columns eliminated in shared memory, one rank-16
+// update of the block's other columns per panel.
 #include <algorithm>
 #include <climits>
 
@@ -348,6 +350,171 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(T* __restrict__ bloc
   }
 }
 
+// Blocks too large for shared memory (nb = 420 at p = 6): Gauss-Jordan by
+// panels of BP columns.  The BP elimination steps of a panel act on any other
+// column x as x <- x + sum_c (X_c - e_{p_c}) x[p_c], where p_c is the pivot row
+// of step c and X_c the panel's column c once the whole panel is eliminated
+// (it is T e_{p_c}, T the product of the panel's steps: a GJ step changes a
+// column only through its entry at the pivot row, and leaves e_i alone for a
+// row i that is not the pivot).  So a panel is eliminated in shared memory
+// (pivot search, the step on the panel's columns) and every other column of
+// the block receives one rank-BP update, read and written once per panel
+// instead of once per step.  Same pivot rule and in-place storage as above;
+// the result is row-major, permuted in place at the end.
+template <class T, int BP>
+__global__ void __launch_bounds__(256) block_inverse_panel_kernel(T* __restrict__ blocks, int nb, size_t bstride,
+                                                                  long nblk, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // byte layout: Pn[nb][BP] | piv_row[nb] | step_of[nb] | used[nb] | lead[nb]
+  T* Pn = reinterpret_cast<T*>(smem_raw);
+  int* piv_row = reinterpret_cast<int*>(Pn + (size_t)nb * BP);
+  int* step_of = piv_row + nb;
+  int* used = step_of + nb;
+  int* lead = used + nb;
+  __shared__ T wv[8], ws[8];
+  __shared__ int wi[8];
+  __shared__ int s_p;
+  __shared__ T s_piv;
+  __shared__ int pr[BP];          // pivot rows of the current panel
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    T* A = blocks + (size_t)blk * bstride;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) used[i] = 0;
+    bool bad = false;
+    for (int k0 = 0; k0 < nb; k0 += BP) {
+      const int bw = min(BP, nb - k0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < nb * BP; t += blockDim.x) {
+        const int i = t / BP, c = t - i * BP;
+        Pn[t] = c < bw ? A[(size_t)i * nb + k0 + c] : T(0);
+      }
+      __syncthreads();
+      for (int c = 0; c < bw; ++c) {
+        const int k = k0 + c;
+        T best = T(-1), sv = T(0);
+        int bi = INT_MAX;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+          const T x = Pn[(size_t)i * BP + c], v = fabs(x) >= T(0) ? fabs(x) : T(0);   // NaN counts as 0
+          if (!used[i] && better(v, i, best, bi)) {
+            best = v;
+            bi = i;
+            sv = x;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T v2 = __shfl_down_sync(0xffffffffu, best, o);
+          const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+          const T s2 = __shfl_down_sync(0xffffffffu, sv, o);
+          if (better(v2, i2, best, bi)) {
+            best = v2;
+            bi = i2;
+            sv = s2;
+          }
+        }
+        if (lane == 0) {
+          wv[warp] = best;
+          wi[warp] = bi;
+          ws[warp] = sv;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          for (int w = 1; w < nw; ++w)
+            if (better(wv[w], wi[w], best, bi)) {
+              best = wv[w];
+              bi = wi[w];
+              sv = ws[w];
+            }
+          s_p = bi;
+          s_piv = sv;
+          piv_row[k] = bi;
+          step_of[bi] = k;
+          used[bi] = 1;
+          pr[c] = bi;
+        }
+        __syncthreads();
+        const int p = s_p;
+        T piv = s_piv;
+        if (!(fabs(piv) > T(0))) {
+          bad = true;
+          piv = T(1);
+        }
+        const T ipiv = T(1) / piv;
+        // the step on the panel's columns, a thread per row i != p (the pivot
+        // row keeps its old values until every other row has used them)
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+          if (i == p) continue;
+          T* pi = Pn + (size_t)i * BP;
+          const T* pp = Pn + (size_t)p * BP;
+          const T m = pi[c];
+          for (int cc = 0; cc < bw; ++cc) pi[cc] = cc == c ? -m * ipiv : pi[cc] - m * pp[cc] * ipiv;
+        }
+        __syncthreads();
+        for (int cc = threadIdx.x; cc < bw; cc += blockDim.x)
+          Pn[(size_t)p * BP + cc] = cc == c ? ipiv : Pn[(size_t)p * BP + cc] * ipiv;
+        __syncthreads();
+      }
+      // every other column: x <- x + sum_c (X_c - e_{p_c}) x[p_c], a thread per column
+      for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+        if (j >= k0 && j < k0 + bw) continue;
+        T xp[BP];
+#pragma unroll
+        for (int c = 0; c < BP; ++c) xp[c] = c < bw ? A[(size_t)pr[c] * nb + j] : T(0);
+        for (int i = 0; i < nb; ++i) {
+          const T* pi = Pn + (size_t)i * BP;
+          T acc = A[(size_t)i * nb + j];
+#pragma unroll
+          for (int c = 0; c < BP; ++c) acc += (pi[c] - (i == pr[c] ? T(1) : T(0))) * xp[c];
+          A[(size_t)i * nb + j] = acc;
+        }
+      }
+      for (int t = threadIdx.x; t < nb * bw; t += blockDim.x) {
+        const int i = t / bw, c = t - i * bw;
+        A[(size_t)i * nb + k0 + c] = Pn[(size_t)i * BP + c];
+      }
+    }
+    // in place: the row permutation i -> step_of[i], then the column
+    // permutation j -> piv_row[j], each applied cycle by cycle
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* to = pass == 0 ? step_of : piv_row;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < nb; ++i) used[i] = 0;
+        for (int i0 = 0; i0 < nb; ++i0) {
+          lead[i0] = 0;
+          if (used[i0]) continue;
+          int c = i0, len = 0;
+          do {
+            used[c] = 1;
+            c = to[c];
+            ++len;
+          } while (c != i0 && len <= nb);
+          lead[i0] = len > 1 ? len : 0;
+        }
+      }
+      __syncthreads();
+      for (int i0 = 0; i0 < nb; ++i0) {
+        const int len = lead[i0];
+        if (len == 0) continue;
+        for (int x = threadIdx.x; x < nb; x += blockDim.x) {
+          const size_t str = pass == 0 ? (size_t)nb : 1, off = pass == 0 ? (size_t)x : (size_t)x * nb;
+          T carry = A[off + (size_t)i0 * str];
+          int src = i0;
+          for (int s = 0; s < len; ++s) {
+            const int dst = to[src];
+            const T y = A[off + (size_t)dst * str];
+            A[off + (size_t)dst * str] = carry;
+            carry = y;
+            src = dst;
+          }
+        }
+      }
+    }
+    if (bad && threadIdx.x == 0) atomicOr(status, ST_SINGULAR);
+    __syncthreads();
+  }
+}
+
 template <class T, int R>
 cudaError_t run_reg(T* A, int nb, size_t bstride, long nblk, int* status, cudaStream_t st) {
   const size_t smem = (size_t)nb * inv_ld<T>(nb) * sizeof(T);
@@ -385,6 +552,20 @@ cudaError_t launch_block_inverse(T* A, int nb, size_t bstride, long nblk, int* s
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const int use_smem = full <= (size_t)smax - 1024;
+  if (!use_smem) {   // panels of 16 columns in shared memory, rank-16 updates of the rest in global memory
+    constexpr int BP = 16;
+    const size_t psm = (size_t)nb * BP * sizeof(T) + 4 * (size_t)nb * sizeof(int);
+    if (psm <= (size_t)smax - 1024) {
+      if (psm > 48 * 1024) allow_max_smem(block_inverse_panel_kernel<T, BP>);
+      int occ = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_inverse_panel_kernel<T, BP>, 256, psm);
+      const long grid = std::min<long>(nblk, (long)std::max(1, occ) * num_sms_inv());
+      *transposed = 0;
+      note_launch();
+      block_inverse_panel_kernel<T, BP><<<(int)grid, 256, psm, st>>>(A, nb, bstride, nblk, status);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = use_smem ? full : base;
   if (smem > 48 * 1024)
     allow_max_smem(block_inverse_kernel<T>);

@@ -5,8 +5,7 @@
 // memory up front, or a time-critical loop that must not enter the CUDA
 // allocator (it may synchronise the device or take a global lock).  This entry
 // point serves them.  It computes exactly what dg_residual computes, with the
-// same face kernel and (for the total-degree space P_p) the same volume
-// kernel, but the face-slot scratch lives in one file-scope device array of
+// same face kernel and the direct volume kernel, but the face-slot scratch lives in one file-scope device array of
 // fixed size instead of in the mesh handle.  The array belongs to this file's
 // device module, which the CUDA runtime may load lazily (on first use):
 // dg_mesh_create looks the array up on its device, so the module and the
@@ -20,9 +19,9 @@
 //  - dg_mesh_create looks up the array's device address (cudaGetSymbolAddress)
 //    on its current device, once per device; a device whose first mesh handle
 //    cannot load the array fails there with DG_ERR_OOM, not here;
-//  - on a mesh of the tensor-product space Q_p, dg_residual evaluates the
-//    volume term by sum factorisation and this entry point by the direct
-//    contractions: the two results agree to rounding, not bit for bit;
+//  - on 3-D meshes and on Q_p meshes dg_residual evaluates the volume term by
+//    sum factorisation and this entry point by the direct contractions: the
+//    two results agree to rounding, not bit for bit;
 //  - all calls share the array: calls that can overlap on the GPU (different
 //    streams without ordering between them) race; order them on one stream;
 //  - the array keeps the last call's contents; no part of it needs to start

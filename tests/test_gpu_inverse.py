@@ -1,6 +1,7 @@
 """Batched element-block inverses (block Jacobi, Sec. 6.3) on every kernel path:
 register tiles (n_b <= 176 in FP32, <= 128 in FP64), the block in shared
-memory, and in place in global memory.  The exported inverse times the
+memory, and in place in global memory by panels of 16 columns (rank-16
+updates; n_b = 175 in FP64, 280 and 420 in both precisions).  The exported inverse times the
 exported (un-inverted) block of the same handle must be the identity.
 
 Bars: FP64 1e-10 in max-norm (Gauss-Jordan with partial pivoting loses about
@@ -21,10 +22,12 @@ pytestmark = pytest.mark.gpu
 CASES = [
     ("tgv3d_p1_fp64", wl.make_config("tgv", 3, (2, 2, 3), 1, M=0.3, Re=100.0), B.PREC_FP64),     # 20, registers
     ("tgv3d_p3_fp64", wl.make_config("tgv", 3, (2, 2, 2), 3, M=0.3, Re=100.0), B.PREC_FP64),     # 100, registers
-    ("tgv3d_p4_fp64", wl.make_config("tgv", 3, (2, 2, 2), 4, M=0.1, Re=1600.0), B.PREC_FP64),    # 175, global
+    ("tgv3d_p4_fp64", wl.make_config("tgv", 3, (2, 2, 2), 4, M=0.1, Re=1600.0), B.PREC_FP64),    # 175, panels
     ("tgv3d_p4_mixed", wl.make_config("tgv", 3, (2, 2, 2), 4, M=0.1, Re=1600.0), B.PREC_MIXED),  # 175, registers
     ("vortex2d_p8_mixed", wl.make_config("vortex", 2, (3, 2), 8, M=0.5, Re=1000.0), B.PREC_MIXED),  # 180, shared
-    ("tgv3d_p5_mixed", wl.make_config("tgv", 3, (2, 1, 2), 5, M=0.1, Re=400.0), B.PREC_MIXED),   # 280, global
+    ("tgv3d_p5_mixed", wl.make_config("tgv", 3, (2, 1, 2), 5, M=0.1, Re=400.0), B.PREC_MIXED),   # 280, panels
+    ("tgv3d_p6_mixed", wl.make_config("tgv", 3, (2, 2, 1), 6, M=0.05, Re=1600.0), B.PREC_MIXED),  # 420, panels
+    ("tgv3d_p6_fp64", wl.make_config("tgv", 3, (1, 2, 2), 6, M=0.05, Re=1600.0), B.PREC_FP64),    # 420, panels
 ]
 
 

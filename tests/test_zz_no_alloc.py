@@ -6,9 +6,10 @@ time-critical loop kept out of the CUDA allocator) call dg_residual_noalloc,
 which keeps its face scratch in a fixed device array inside the library.  This
 test calls it through the C ABI twice in a row and checks each result against
 dg_residual (same kernels, so within the residual tolerance of the parity
-tests, 1e-12 relative max-norm), including a mesh of the tensor-product space
-Q_p (where dg_residual sums the volume term by factorisation and this entry
-point takes the direct contractions: equal to rounding); that repeated calls
+tests, 1e-12 relative max-norm; on 3-D meshes and on the tensor-product
+space Q_p, which a case here uses, dg_residual sums the volume term by
+factorisation and this entry point takes the direct contractions: equal to
+rounding); that repeated calls
 leave the device's free memory unchanged and launch only the face and volume
 kernels; and that an oversized mesh is refused.  The file is collected last
 so that a failure here leaves every other test run.
