@@ -507,7 +507,7 @@ def kernel_rooflines(torch, B, mixed, fp64, stream, peaks, ref_cfg):
     if fp64 is not None:
         alu("face_kernel<3,double,1> (outer JVP, faces; FP64)", fp64, B.KT_FACE_JVP, "face_jvp_fp64",
             FP64_PEAK_TFLOPS, "f64")
-        alu("volume_kernel<3,double,1> (outer JVP, volume; FP64)", fp64, B.KT_VOLUME_JVP, "volume_jvp_fp64",
+        alu("volume_q_kernel<3,double,1> (outer JVP, volume by sum factorisation; FP64)", fp64, B.KT_VOLUME_JVP, "volume_jvp_fp64",
             FP64_PEAK_TFLOPS, "f64")
     # block-Jacobi apply of the fine level (FP32 inverses, column-major, padded rows)
     ld = (nb + 3) // 4 * 4
@@ -529,7 +529,7 @@ def kernel_rooflines(torch, B, mixed, fp64, stream, peaks, ref_cfg):
         ms = mixed.pmg.kernel_time(B.KT_SMOOTH, 1, 5, stream=stream)
         nf = 2 * len(mixed.cfg["n"])
         by = E * nb1 * ld1 * 4 * ((nu + 1) * (1 + nf) + nu) + E * nb1 * 4 * (4 + 2 * nu)
-        out.append({"kernel": "coop_smooth_kernel<float> (one smoother call, level 1, %d iterations)" % nu,
+        out.append({"kernel": "coop_smooth_kernel<float,6> (one smoother call, level 1, %d iterations)" % nu,
                     "bound": "hbm", "dtype": "f32", "achieved": by / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": by / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
                     "ms": ms, "algorithmic_bytes": by})
