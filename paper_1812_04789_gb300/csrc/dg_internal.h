@@ -135,6 +135,14 @@ template <class T>
 cudaError_t launch_volume_q(const Mesh& M, const T* W, const T* V, const T* S, T sigma, bool jvp, T* out,
                             cudaStream_t st);
 
+// Face term (the face slots) of the residual or exact JVP on a 3-D structured
+// mesh by sum factorisation (csrc/dg_face_sf.cu); same contract as the face
+// kernel of launch_residual (Pf: cached primal face traces, FP32 JVP only).
+// cudaErrorNotSupported when the mesh is not 3-D or the stages do not fit.
+template <class T>
+cudaError_t launch_face_sf(const Mesh& M, const T* W, const T* V, T* slots, bool jvp, const T* Pf,
+                           cudaStream_t st);
+
 // Primal traces (u, grad u) of an FP32 state at the volume points and on both
 // sides of every face point; primal_cache_sizes returns the volume cache's
 // length and sets the face cache's (floats).

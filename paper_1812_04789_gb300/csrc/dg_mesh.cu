@@ -352,13 +352,19 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
     return err == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
   {   // one-dimensional factors for sum factorisation (Q_p, and P_p embedded in Q_p)
     const int n1 = p + 1;
-    std::vector<double> l1d((size_t)2 * n1 * nq1 + nq1);
+    // layout: L[a][q], dL[a][q] (reference derivative), w[q], then the end
+    // values L_a(-1), L_a(+1) and dL_a(-1), dL_a(+1) (face traces)
+    std::vector<double> l1d((size_t)2 * n1 * nq1 + nq1 + 4 * n1);
     for (int a = 0; a < n1; ++a)
       for (int q = 0; q < nq1; ++q) {
         l1d[(size_t)a * nq1 + q] = L1(q, a);
         l1d[(size_t)(n1 + a) * nq1 + q] = dL1(q, a);
       }
     for (int q = 0; q < nq1; ++q) l1d[(size_t)2 * n1 * nq1 + q] = wg[q];
+    for (int a = 0; a < 2 * n1; ++a) {
+      l1d[(size_t)2 * n1 * nq1 + nq1 + a] = Le[a];
+      l1d[(size_t)2 * n1 * nq1 + nq1 + 2 * n1 + a] = dLe[a];
+    }
     if ((err = upload<double>(M, l1d, &M.t64.l1d)) != cudaSuccess) return DG_ERR_OOM;
     if ((err = upload<float>(M, l1d, &M.t32.l1d)) != cudaSuccess) return DG_ERR_OOM;
     int nt = 1;
