@@ -505,7 +505,7 @@ def kernel_rooflines(torch, B, mixed, fp64, stream, peaks, ref_cfg):
     alu("volume_kernel_st<3,1,3> (smoother JVP, volume; FP32, tables in shared memory)", mixed, B.KT_VOLUME_JVP,
         "volume_jvp_fp32", FP32_PEAK_TFLOPS, "f32")
     if fp64 is not None:
-        alu("face_kernel<3,double,1> (outer JVP, faces; FP64)", fp64, B.KT_FACE_JVP, "face_jvp_fp64",
+        alu("face_sf_kernel<double,1> (outer JVP, faces by sum factorisation; FP64)", fp64, B.KT_FACE_JVP, "face_jvp_fp64",
             FP64_PEAK_TFLOPS, "f64")
         alu("volume_q_kernel<3,double,1> (outer JVP, volume by sum factorisation; FP64)", fp64, B.KT_VOLUME_JVP, "volume_jvp_fp64",
             FP64_PEAK_TFLOPS, "f64")

@@ -41,9 +41,11 @@ template <class T> __host__ __device__ __forceinline__ Dual<T> operator+(Dual<T>
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return Dual<T>(a.v - b.v, a.d - b.d); }
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return Dual<T>(-a.v, -a.d); }
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return Dual<T>(a.v * b.v, a.d * b.v + a.v * b.d); }
+// one division per quotient: the tangent reuses the reciprocal of the value
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
-  T q = a.v / b.v;
-  return Dual<T>(q, (a.d - q * b.d) / b.v);
+  const T r = T(1) / b.v;
+  const T q = a.v * r;
+  return Dual<T>(q, (a.d - q * b.d) * r);
 }
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return Dual<T>(a.v + b, a.d); }
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) { return Dual<T>(a + b.v, b.d); }
@@ -51,14 +53,18 @@ template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(Dual<T>
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return Dual<T>(a - b.v, -b.d); }
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return Dual<T>(a.v * b, a.d * b); }
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return Dual<T>(a * b.v, a * b.d); }
-template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return Dual<T>(a.v / b, a.d / b); }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) {
+  const T r = T(1) / b;
+  return Dual<T>(a.v * r, a.d * r);
+}
 template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
-  T q = a / b.v;
-  return Dual<T>(q, -q * b.d / b.v);
+  const T r = T(1) / b.v;
+  const T q = a * r;
+  return Dual<T>(q, -q * b.d * r);
 }
 template <class T> __host__ __device__ __forceinline__ Dual<T> dsqrt(Dual<T> a) {
-  T s = sqrt(a.v);
-  return Dual<T>(s, a.d / (T(2) * s));
+  const T s = sqrt(a.v);
+  return Dual<T>(s, a.d * (T(0.5) / s));
 }
 __host__ __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 __host__ __device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
