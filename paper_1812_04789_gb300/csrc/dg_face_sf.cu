@@ -38,17 +38,16 @@ __host__ __device__ inline FsfPlan fsf_plan(int p, int nq, int nb, int M, bool j
   P.nqf = nq * nq;
   const bool haveW = !(jvp && cached);
   P.NC = (haveW ? 1 : 0) + (jvp ? 1 : 0);
-  size_t o = 0;
-  P.oW = o;
-  o += haveW ? (size_t)fpc * 2 * nb : 0;
-  P.oV = o;
-  o += jvp ? (size_t)fpc * 2 * nb : 0;
-  P.oG = o;
-  o += (size_t)fpc * 2 * P.nqf * M;
-  P.oF = o;
-  o += (size_t)fpc * P.nqf * M;
-  P.oD = o;
-  o += (size_t)fpc * 2 * P.nqf * M * 3;
+  // the coefficients (read by S1 only) share their space with the point values
+  // (written from phase 1 on, after S2)
+  P.oW = 0;
+  P.oV = haveW ? (size_t)fpc * 2 * nb : 0;
+  const size_t coef = P.oV + (jvp ? (size_t)fpc * 2 * nb : 0);
+  P.oG = 0;
+  P.oF = (size_t)fpc * 2 * P.nqf * M;
+  P.oD = P.oF + (size_t)fpc * P.nqf * M;
+  const size_t pts = P.oD + (size_t)fpc * 2 * P.nqf * M * 3;
+  size_t o = coef > pts ? coef : pts;
   const size_t interp = (size_t)2 * P.NC * M * (2 * P.n1 * P.n1 + 3 * P.n1 * nq);
   const size_t proj = (size_t)2 * M * (3 * P.n1 * nq + 2 * P.n1 * P.n1);
   P.per_face = interp > proj ? interp : proj;
@@ -69,7 +68,7 @@ __device__ __forceinline__ T pick3(int d, T x0, T x1, T x2) {
 }  // namespace
 
 template <class T, bool JVP>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
     face_sf_kernel(MeshView<T> mv, Phys<T> ph, const T* __restrict__ W, const T* __restrict__ V,
                    T* __restrict__ slots, int* status, int fpc, const T* __restrict__ Pf, const T* __restrict__ l1g,
                    const int* __restrict__ qidx, int p, int nq, T m0, T m1, T m2) {
@@ -84,8 +83,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
   const bool haveW = !cached;
   const int nfaces = D * E, f0 = blockIdx.x * fpc, nloc = min(fpc, nfaces - f0);
   if (nloc <= 0) return;
-  T* sW = sm + P.oW;               // [fpc][2][nb]  state (not with cached traces)
-  T* sV = sm + P.oV;               // [fpc][2][nb]  direction (JVP)
+  T* sW = sm + P.oW;               // [fpc][2][nb]  state (not with cached traces), until S1
+  T* sV = sm + P.oV;               // [fpc][2][nb]  direction (JVP), until S1
   T* sG = sm + P.oG;               // [fpc][2][nqf][M]
   T* sF = sm + P.oF;               // [fpc][nqf][M]
   T* sD = sm + P.oD;               // [fpc][2][nqf][M][D]

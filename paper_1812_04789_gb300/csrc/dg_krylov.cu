@@ -7,6 +7,16 @@
 // on timing.  The Hessenberg column, the Givens rotations, the least-squares
 // solve and the residual estimate |g_{j+1}| live in device memory; the host
 // never waits on them unless it asks for the residual.
+//
+// FP32 vectors (the smoothers of the mixed-precision preconditioner) take
+// their per-entry arithmetic in FP32 and only the sums across threads and
+// CTAs in FP64: GB300 executes FP64 (and FP32<->FP64 conversions) at a small
+// fraction of its FP32 rate, so a per-entry FP64 multiply-add made these
+// kernels FP64-bound.  The inner products sum at most 16 FP32 products per
+// thread before an FP64 add; the coefficients of w -= V c and x += Z y are
+// rounded to FP32 once per CTA.  Classical Gram-Schmidt applied twice keeps
+// the basis orthogonal to working precision with FP32 subtraction: the second
+// pass removes what the rounding of the first left along V.
 #include <math.h>
 
 #include <algorithm>
@@ -127,6 +137,33 @@ __global__ void __launch_bounds__(256) mdot_kernel(const T* __restrict__ V, long
   }
   if (threadIdx.x == 0) part[(size_t)i * G + c] = red[0];
 }
+template <>
+__global__ void __launch_bounds__(256) mdot_kernel<float>(const float* __restrict__ V, long N,
+                                                          const float* __restrict__ w, int G,
+                                                          double* __restrict__ part) {
+  __shared__ double red[256];
+  const int i = blockIdx.y, c = blockIdx.x;
+  const long chunk = (N + G - 1) / G;
+  const long beg = c * chunk, end = min(N, beg + chunk);
+  const float* v = V + (size_t)i * N;
+  double s = 0.0;
+  for (long n0 = beg + threadIdx.x; n0 < end; n0 += 16L * blockDim.x) {
+    float f = 0.f;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const long n = n0 + (long)u * blockDim.x;
+      if (n < end) f = fmaf(v[n], w[n], f);
+    }
+    s += (double)f;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)i * G + c] = red[0];
+}
 
 // mode 0: H[i][j] = sum; mode 1: H[i][j] += sum;  (one warp per i, fixed order)
 __global__ void finalize_dots_kernel(const double* __restrict__ part, int G, int nvec, double* __restrict__ Hcol,
@@ -155,6 +192,20 @@ __global__ void subtract_kernel(const T* __restrict__ V, long N, const double* _
     double acc = (double)w[n];
     for (int i = 0; i < nvec; ++i) acc -= c[i] * (double)V[(size_t)i * N + n];
     w[n] = (T)acc;
+  }
+}
+// FP32: the coefficients rounded once into shared memory (nvec <= KMAX_F32)
+constexpr int KMAX_F32 = 128;
+template <>
+__global__ void subtract_kernel<float>(const float* __restrict__ V, long N, const double* __restrict__ c, int nvec,
+                                       float* __restrict__ w) {
+  __shared__ float cf[KMAX_F32];
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) cf[i] = (float)c[i];
+  __syncthreads();
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    float acc = w[n];
+    for (int i = 0; i < nvec; ++i) acc = fmaf(-cf[i], V[(size_t)i * N + n], acc);
+    w[n] = acc;
   }
 }
 
@@ -188,6 +239,13 @@ __global__ void scale_kernel(long N, const T* __restrict__ x, const double* __re
   double a = *inv;
   for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
     y[n] = (T)(a * (double)x[n]);
+}
+template <>
+__global__ void scale_kernel<float>(long N, const float* __restrict__ x, const double* __restrict__ inv,
+                                    float* __restrict__ y) {
+  const float a = (float)*inv;
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x)
+    y[n] = a * x[n];
 }
 
 // Givens update of Hessenberg column j (column-major, ld = nmax+1).
@@ -241,6 +299,19 @@ __global__ void update_kernel(const T* __restrict__ Z, long N, const double* __r
     x[n] = (T)acc;
   }
 }
+template <>
+__global__ void update_kernel<float>(const float* __restrict__ Z, long N, const double* __restrict__ y, int k,
+                                     const int* __restrict__ kdim, float* __restrict__ x) {
+  __shared__ float yf[KMAX_F32];
+  k = min(k, *kdim);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) yf[i] = (float)y[i];
+  __syncthreads();
+  for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < N; n += (long)gridDim.x * blockDim.x) {
+    float acc = x[n];
+    for (int i = 0; i < k; ++i) acc = fmaf(yf[i], Z[(size_t)i * N + n], acc);
+    x[n] = acc;
+  }
+}
 
 __global__ void set_int_kernel(int* p, int v) { *p = v; }
 
@@ -248,6 +319,7 @@ __global__ void set_int_kernel(int* p, int v) { *p = v; }
 template <class T>
 cudaError_t Krylov<T>::alloc(long n, int nm) {
   release();
+  if (sizeof(T) == sizeof(float) && nm + 1 > KMAX_F32) return cudaErrorInvalidValue;
   N = n;
   nmax = nm;
   G = (int)std::max<long>(1, std::min<long>(2L * sm_count(), (n + 1023) / 1024));

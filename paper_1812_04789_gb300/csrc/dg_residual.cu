@@ -488,10 +488,13 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
     // 3-D: the face term by sum factorisation in FP64 (fewer of the FP64 pipe's
     // cycles: the residual 4.5 -> 3.8 ms at 16^3 p = 4) and in FP32 above 40
     // modes (at p = 4 the direct FP32 kernel is faster: 0.39 against 0.57 ms);
-    // DG_NO_SUMFACT_FACE=1 keeps the direct kernel
+    // DG_NO_SUMFACT_FACE=1 keeps the direct kernel, DG_SUMFACT_FACE_MIN_MODES
+    // moves the FP32 threshold (41 modes)
     const char* nsff = getenv("DG_NO_SUMFACT_FACE");
+    const char* sfmin = getenv("DG_SUMFACT_FACE_MIN_MODES");
+    const int min_modes = sfmin ? atoi(sfmin) : 41;
     cudaError_t e = cudaErrorNotSupported;
-    if (D == 3 && !(nsff && nsff[0] == '1') && (std::is_same<T, double>::value || Ms.nm > 40)) {
+    if (D == 3 && !(nsff && nsff[0] == '1') && (std::is_same<T, double>::value || Ms.nm >= min_modes)) {
       e = launch_face_sf<T>(Ms, W, V, slots, JVP, JVP ? Pf : nullptr, st);
       if (e == cudaErrorNotSupported) (void)cudaGetLastError();
     }

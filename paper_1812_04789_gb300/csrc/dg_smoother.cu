@@ -12,12 +12,21 @@
 // iteration j:
 //   A  v_j = w / ||w||; z_j = D^{-1} v_j (own elements)                 | grid barrier
 //   B  w = A z_j (own elements, neighbours' z_j read); partial V^T w    | grid barrier
-//   C  h1 = sum of partials; w -= V h1; partial V^T w                    | grid barrier
-//   D  h2 = sum of partials; w -= V h2; partial ||w||^2                  | grid barrier
-// (CGS2, as the launch-per-operation Arnoldi).  Every CTA sums the partials
+//   C  h1 = sum of partials; w -= V h1; partial V^T w and ||w||^2       | grid barrier
+//   D  h2 = sum of partials; w -= V h2; ||w - V h2||^2 = ||w||^2 - ||h2||^2
+// (CGS2, as the launch-per-operation Arnoldi; the norm after the second pass
+// by Pythagoras, as in the low-synchronisation Gram-Schmidt variants of
+// Swirydowicz et al. 2021, which saves a barrier: h2 is at rounding level
+// against w, so the difference loses nothing.  Where it would cancel, more
+// than 99 % of ||w||^2, the norm is summed explicitly behind a fourth
+// barrier; every CTA takes the same branch.)  Every CTA sums the partials
 // of all CTAs in the same fixed order and keeps its own copy of the
 // Hessenberg matrix, the Givens rotations and g, so all CTAs hold identical
-// scalars and the final x += Z y needs no further barrier.
+// scalars and the final x += Z y needs no further barrier.  The per-row
+// arithmetic is FP32 (products, w -= V h with h rounded to FP32, x += Z y):
+// GB300 runs FP64 and FP32<->FP64 conversions at a small fraction of its FP32
+// rate, and per-row FP64 made the smoother FP64-bound; only the sums across
+// rows, warps and CTAs are FP64.
 //
 // The grid barrier counts arrivals in one word and releases the waiting CTAs
 // through another (its own 128-byte line, so the polls do not contend with
@@ -125,13 +134,22 @@ __device__ double block_sum(double s, double* red) {
   return t;
 }
 
-// out[i] = sum over the CTA's rows of V_i . w (shared memory), i < nv, warp per i
+// out[i] = sum over the CTA's rows of V_i . w (shared memory), i < nv, warp per
+// i; FP32 products summed 16 at a time, then in FP64
 __device__ void own_dots(int nv, const float* Vs, int ldv, const float* ws, int rows, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < nv; i += nw) {
     const float* v = Vs + (size_t)i * ldv;
     double s = 0.0;
-    for (int r = lane; r < rows; r += 32) s += (double)v[r] * (double)ws[r];
+    for (int r0 = lane; r0 < rows; r0 += 16 * 32) {
+      float f = 0.f;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int r = r0 + 32 * u;
+        if (r < rows) f = fmaf(v[r], ws[r], f);
+      }
+      s += (double)f;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[i] = s;
@@ -263,7 +281,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
   double* red = h2 + ldh;                             // 32
   int* sflag = reinterpret_cast<int*>(red + 32);      // 4 ints
   const int rmax = a.chunk * nb;
-  float* Vs = reinterpret_cast<float*>(sflag + 4);    // [nu + 1][rmax]
+  float* hf = reinterpret_cast<float*>(sflag + 4);    // [nu + 1] coefficients rounded to FP32
+  float* Vs = hf + ((ldh + 3) & ~3);                  // [nu + 1][rmax]
   float* Zs = Vs + (size_t)ldh * rmax;                // [nu][rmax]
   float* ws = Zs + (size_t)nu * rmax;                 // [rmax]
   float* xs = ws + rmax;                              // [epc][1 + nf][nb]
@@ -283,9 +302,9 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
   // r = b - A x into w, ||r||^2
   bsr_own<S, NF>(a, a.x, a.b, ws, e_beg, ne, xs);
   {
-    double s = 0.0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += (double)ws[r] * (double)ws[r];
-    s = block_sum(s, red);
+    float f = 0.f;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) f = fmaf(ws[r], ws[r], f);
+    const double s = block_sum((double)f, red);
     if (threadIdx.x == 0) mypart[2 * ldh] = s;
   }
   if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
@@ -304,7 +323,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
   for (int j = 0; j < nu; ++j) {
     // A: v_j = w / ||w||, z_j = D^{-1} v_j
     float* vj = Vs + (size_t)j * rmax;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) vj[r] = (float)(inv * (double)ws[r]);
+    const float finv = (float)inv;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) vj[r] = finv * ws[r];
     __syncthreads();
     float* zg = a.Z + (size_t)j * N;
     bj_own<S>(a, vj, Zs + (size_t)j * rmax, zg, e_beg, ne);
@@ -313,31 +333,55 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
     bsr_own<S, NF>(a, zg, nullptr, ws, e_beg, ne, xs);
     own_dots(j + 1, Vs, rmax, ws, rows, mypart);
     if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
-    // C: w -= V h1, second pass
+    // C: w -= V h1; second pass of inner products and ||w||^2 (at mypart[ldh + j + 1])
     sum_parts(j + 1, a.part, stride, G, h1);
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-      double acc = (double)ws[r];
-      for (int i = 0; i <= j; ++i) acc -= h1[i] * (double)Vs[(size_t)i * rmax + r];
-      ws[r] = (float)acc;
-    }
+    if (threadIdx.x <= j) hf[threadIdx.x] = (float)h1[threadIdx.x];
     __syncthreads();
-    own_dots(j + 1, Vs, rmax, ws, rows, mypart + ldh);
-    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
-    // D: w -= V h2, ||w||^2
-    sum_parts(j + 1, a.part + ldh, stride, G, h2);
-    double s = 0.0;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-      double acc = (double)ws[r];
-      for (int i = 0; i <= j; ++i) acc -= h2[i] * (double)Vs[(size_t)i * rmax + r];
-      const float wf = (float)acc;
-      ws[r] = wf;
-      s += (double)wf * (double)wf;
+    {
+      float f = 0.f;
+      for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        float acc = ws[r];
+        for (int i = 0; i <= j; ++i) acc = fmaf(-hf[i], Vs[(size_t)i * rmax + r], acc);
+        ws[r] = acc;
+        f = fmaf(acc, acc, f);
+      }
+      const double s = block_sum((double)f, red);
+      own_dots(j + 1, Vs, rmax, ws, rows, mypart + ldh);
+      if (threadIdx.x == 0) mypart[ldh + j + 1] = s;
     }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) mypart[2 * ldh] = s;
     if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
-    sum_parts(1, a.part + 2 * ldh, stride, G, red + 16);   // red[16] = ||w||^2 (red[0..15] free here)
-    const double hn = sqrt(red[16]);
+    // D: w -= V h2, ||w - V h2|| from ||w||^2 - ||h2||^2
+    sum_parts(j + 2, a.part + ldh, stride, G, h2);   // h2[j + 1] = ||w||^2
+    if (threadIdx.x == 0) {
+      double hs = 0.0;
+      for (int i = 0; i <= j; ++i) hs += h2[i] * h2[i];
+      red[17] = h2[j + 1] - hs;
+    }
+    if (threadIdx.x <= j) hf[threadIdx.x] = (float)h2[threadIdx.x];
+    __syncthreads();
+    const double nw2 = h2[j + 1], hn2 = red[17];
+    const bool explicit_norm = !(hn2 >= 0.01 * nw2);   // cancellation (or not finite): sum it
+    {
+      float f = 0.f;
+      for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        float acc = ws[r];
+        for (int i = 0; i <= j; ++i) acc = fmaf(-hf[i], Vs[(size_t)i * rmax + r], acc);
+        ws[r] = acc;
+        f = fmaf(acc, acc, f);
+      }
+      if (explicit_norm) {
+        const double s = block_sum((double)f, red);
+        if (threadIdx.x == 0) mypart[2 * ldh] = s;
+      }
+    }
+    double hn;
+    if (explicit_norm) {
+      if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
+      sum_parts(1, a.part + 2 * ldh, stride, G, red + 16);   // red[16] = ||w||^2 (red[0..15] free here)
+      hn = sqrt(red[16]);
+    } else {
+      hn = sqrt(hn2);
+    }
     // Hessenberg column j, earlier rotations, new rotation, g (every CTA alike)
     if (threadIdx.x == 0) {
       double* h = H + (size_t)j * ldh;
@@ -377,14 +421,15 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
       for (int c = i + 1; c < kdone; ++c) s -= H[(size_t)c * ldh + i] * h1[c];
       const double d = H[(size_t)i * ldh + i];
       h1[i] = d != 0.0 ? s / d : 0.0;
+      hf[i] = (float)h1[i];
     }
   }
   __syncthreads();
   float* xo = a.x + (size_t)e_beg * nb;
   for (int r = threadIdx.x; r < rows; r += blockDim.x) {
-    double acc = (double)xo[r];
-    for (int i = 0; i < kdone; ++i) acc += h1[i] * (double)Zs[(size_t)i * rmax + r];
-    xo[r] = (float)acc;
+    float acc = xo[r];
+    for (int i = 0; i < kdone; ++i) acc = fmaf(hf[i], Zs[(size_t)i * rmax + r], acc);
+    xo[r] = acc;
   }
 }
 
@@ -392,7 +437,7 @@ static size_t coop_smem(int nu, int nb, int nf, int chunk, int epc) {
   const size_t ldh = nu + 1;
   const size_t dbl = ldh * nu + 2 * (size_t)nu + 3 * ldh + 32;
   const size_t rmax = (size_t)chunk * nb;
-  const size_t flt = (2 * (size_t)nu + 2) * rmax + (size_t)epc * (1 + nf) * nb;
+  const size_t flt = ((ldh + 3) & ~(size_t)3) + (2 * (size_t)nu + 2) * rmax + (size_t)epc * (1 + nf) * nb;
   return dbl * sizeof(double) + 4 * sizeof(int) + flt * sizeof(float);
 }
 
