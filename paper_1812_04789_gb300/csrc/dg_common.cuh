@@ -363,10 +363,38 @@ struct MeshView {
   const T* fphi;           // [2d][nqf][nm]
   const T* fdphi;          // [2d][d][nqf][nm]
   const T* fw;             // [d][nqf]    face weights * |J_F|
-  const T* lift;           // [2d][nqf][nqf] BR2 lifting operator (eq. re) incl. 1/(2|J|)
+  const T* lift;           // [2d][nqf q'][nqf q] BR2 lifting operator P[q][q'] (eq. re) incl. 1/(2|J|)
   const T* liftT;          // [2d][2][nqf][nm] lifted test functions of local face f:
                            //   sum_q fw(q) phi_i(q) P[q][q'], P = lift[2k+1] (c=0) or lift[2k] (c=1)
+  const T* fpk;            // [2d][nm][nqf][4] (phi_i, d_0 phi_i, .., d_{d-1} phi_i, 0 ..) at face point q
+  const T* fpw;            // [2d][nqf][nm][4] the same times the face weight fw(q)
   T detJ;
 };
+
+// padded length of a short vector of T in shared memory: a multiple of 16 bytes
+__host__ __device__ constexpr int pad16(int n, int size) { return size == 4 ? ((n + 3) & ~3) : ((n + 1) & ~1); }
+
+// N consecutive values from a 16-byte aligned address (N * sizeof(T) a
+// multiple of 16): 16-byte loads
+template <class T, int N>
+__device__ __forceinline__ void ld_vec(const T* p, T* out) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 t = reinterpret_cast<const float4*>(p)[k];
+      out[4 * k] = t.x;
+      out[4 * k + 1] = t.y;
+      out[4 * k + 2] = t.z;
+      out[4 * k + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      const double2 t = reinterpret_cast<const double2*>(p)[k];
+      out[2 * k] = t.x;
+      out[2 * k + 1] = t.y;
+    }
+  }
+}
 
 }  // namespace dgk

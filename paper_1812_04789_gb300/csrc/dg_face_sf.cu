@@ -225,13 +225,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2)
   for (int t = threadIdx.x; t < nloc * nqf; t += blockDim.x) {
     const int fl = t / nqf, q = t % nqf;
     const int k = (f0 + fl) / E;
-    const T* PL = mv.lift + ((size_t)(2 * k + 1) * nqf + q) * nqf;
-    const T* PR = mv.lift + ((size_t)(2 * k) * nqf + q) * nqf;
+    const T* PL = mv.lift + (size_t)(2 * k + 1) * nqf * nqf + q;   // column q2 at PL[q2 * nqf]
+    const T* PR = mv.lift + (size_t)(2 * k) * nqf * nqf + q;
     T dl[M], dr[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) dl[v] = dr[v] = T(0);
     for (int q2 = 0; q2 < nqf; ++q2) {
-      const T a = PL[q2], b = PR[q2];
+      const T a = PL[(size_t)q2 * nqf], b = PR[(size_t)q2 * nqf];
       const T* g0 = sG + ((size_t)fl * 2 * nqf + q2) * M;
       const T* g1 = sG + ((size_t)(fl * 2 + 1) * nqf + q2) * M;
 #pragma unroll

@@ -41,6 +41,8 @@ struct Tables {
   T *fphiT = nullptr, *fdphiT = nullptr, *fphi = nullptr, *fdphi = nullptr, *fw = nullptr;
   T* lift = nullptr;
   T* liftT = nullptr;        // lifted test tables [2d][2][nqf][nm]
+  T* fpk = nullptr;          // packed face traces [2d][nm][nqf][4]
+  T* fpw = nullptr;          // packed weighted face traces [2d][nqf][nm][4]
   T* slots = nullptr;        // face slots [E][d][2][nb]
   T* fd_w = nullptr;         // finite-difference JVP scratch: W + h v
   T* fd_r = nullptr;         // finite-difference JVP scratch: R(W + h v)

@@ -111,9 +111,9 @@ static cudaError_t upload(Mesh& M, const std::vector<double>& h, T** dst) {
 template <class T>
 static cudaError_t upload_tables(Mesh& M, Tables<T>& t, const std::vector<double>* tabs) {
   cudaError_t e;
-  T** dst[12] = {&t.vphiT, &t.vdphiT, &t.vphi, &t.vdphi, &t.vw, &t.fphiT,
-                 &t.fdphiT, &t.fphi, &t.fdphi, &t.fw, &t.lift, &t.liftT};
-  for (int i = 0; i < 12; ++i)
+  T** dst[14] = {&t.vphiT, &t.vdphiT, &t.vphi, &t.vdphi, &t.vw, &t.fphiT, &t.fdphiT,
+                 &t.fphi,  &t.fdphi,  &t.fw,   &t.lift,  &t.liftT, &t.fpk, &t.fpw};
+  for (int i = 0; i < 14; ++i)
     if ((e = upload<T>(M, tabs[i], dst[i])) != cudaSuccess) return e;
   size_t ns = (size_t)M.E * M.d * 2 * M.nb;
   if ((e = cudaMalloc((void**)&t.slots, ns * sizeof(T))) != cudaSuccess) return e;
@@ -143,6 +143,8 @@ MeshView<double> Mesh::view<double>() const {
   v.fphiT = t64.fphiT; v.fdphiT = t64.fdphiT; v.fphi = t64.fphi; v.fdphi = t64.fdphi; v.fw = t64.fw;
   v.lift = t64.lift;
   v.liftT = t64.liftT;
+  v.fpk = t64.fpk;
+  v.fpw = t64.fpw;
   v.detJ = detJ;
   return v;
 }
@@ -156,6 +158,8 @@ MeshView<float> Mesh::view<float>() const {
   v.fphiT = t32.fphiT; v.fdphiT = t32.fdphiT; v.fphi = t32.fphi; v.fdphi = t32.fdphi; v.fw = t32.fw;
   v.lift = t32.lift;
   v.liftT = t32.liftT;
+  v.fpk = t32.fpk;
+  v.fpw = t32.fpw;
   v.detJ = (float)detJ;
   return v;
 }
@@ -215,7 +219,7 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
   auto dL1 = [&](int a, int deg) { return dL[(size_t)a * (p + 1) + deg]; };
 
   const int nq = M.nq, nqf = M.nqf, nm = M.nm;
-  std::vector<double> tabs[12];
+  std::vector<double> tabs[14];
   std::vector<double>&vphiT = tabs[0], &vdphiT = tabs[1], &vphi = tabs[2], &vdphi = tabs[3], &vw = tabs[4];
   std::vector<double>&fphiT = tabs[5], &fdphiT = tabs[6], &fphi = tabs[7], &fdphi = tabs[8], &fw = tabs[9];
   std::vector<double>& lift = tabs[10];
@@ -295,14 +299,15 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
       }
     }
     // BR2 lifting at face points (eq. re): delta(q) = |J_F|/(2|J|) sum_i phi_i(q)
-    // sum_q' w_q' phi_i(q') X(q')  =>  lift[f][q][q'] (mass matrix |J| I)
+    // sum_q' w_q' phi_i(q') X(q')  =>  P_f[q][q'] (mass matrix |J| I), stored by
+    // columns, lift[f][q'][q]: a warp's points q of one column are consecutive
     double cl = M.faceJ[k] / (2.0 * M.detJ);
     for (int q = 0; q < nqf; ++q)
       for (int q2 = 0; q2 < nqf; ++q2) {
         double s = 0;
         for (int i = 0; i < nm; ++i)
           s += fphi[((size_t)f * nqf + q) * nm + i] * fphi[((size_t)f * nqf + q2) * nm + i];
-        lift[((size_t)f * nqf + q) * nqf + q2] = cl * s * wraw[q2];
+        lift[((size_t)f * nqf + q2) * nqf + q] = cl * s * wraw[q2];
       }
   }
   // lifted test functions: the BR2 term sum_q fw(q) phi_i(q) {delta}(q) is linear
@@ -319,11 +324,28 @@ static dg_status build_mesh(Mesh& M, const dg_mesh_desc* desc, const dg_physics*
           double s = 0;
           for (int q = 0; q < nqf; ++q)
             s += fw[(size_t)k * nqf + q] * fphi[((size_t)f * nqf + q) * nm + i] *
-                 lift[((size_t)pf * nqf + q) * nqf + q2];
+                 lift[((size_t)pf * nqf + q2) * nqf + q];
           liftT[(((size_t)f * 2 + c) * nqf + q2) * nm + i] = s;
         }
     }
   }
+  // packed traces for 16-byte loads: fpk[f][i][q] = (phi, grad phi) at point q,
+  // fpw[f][q][i] = fw(q) (phi, grad phi)
+  std::vector<double>&fpk = tabs[12], &fpw = tabs[13];
+  fpk.assign((size_t)nf * nm * nqf * 4, 0);
+  fpw.assign((size_t)nf * nqf * nm * 4, 0);
+  for (int f = 0; f < nf; ++f)
+    for (int q = 0; q < nqf; ++q) {
+      const double wq = fw[(size_t)(f / 2) * nqf + q];
+      for (int i = 0; i < nm; ++i) {
+        double e[4] = {fphi[((size_t)f * nqf + q) * nm + i], 0, 0, 0};
+        for (int kk = 0; kk < d; ++kk) e[1 + kk] = fdphi[(((size_t)f * d + kk) * nqf + q) * nm + i];
+        for (int c = 0; c < 4; ++c) {
+          fpk[(((size_t)f * nm + i) * nqf + q) * 4 + c] = e[c];
+          fpw[(((size_t)f * nqf + q) * nm + i) * 4 + c] = wq * e[c];
+        }
+      }
+    }
   // neighbours
   std::vector<int> nbr((size_t)M.E * d * 2);
   for (int e = 0; e < M.E; ++e) {

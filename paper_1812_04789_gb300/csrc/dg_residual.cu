@@ -17,6 +17,7 @@
 // With S = Dual<T> the same code carries the directional derivative: the JVP
 // is the exact linearisation of the discrete residual.
 #include <algorithm>
+#include <climits>
 #include <cstdlib>
 #include <type_traits>
 
@@ -30,6 +31,15 @@ __device__ __forceinline__ int dof(int nm, int v, int i) {
 }
 
 // ---------------------------------------------------------------- face kernel
+// Shared memory per face (MP = M, DP = M d, each padded to 16 bytes):
+//   sW, sV [2][nm][MP]  coefficients of both elements, mode-major (one mode's M
+//                       variables in one or two 16-byte loads)
+//   sG [2][nqf][MP]     normal column of K(u)(jump n), both sides
+//   sF [nqf][MP]        flux (Roe + averaged F_v, + lifting)
+//   sD [2][nqf][DP]     dual-consistency tensors / 2, both sides
+// The trace tables are packed (phi, grad phi) per mode and point (fpk, and
+// fpw with the face weight folded in for the projection), so a mode costs one
+// 16-byte table load per side.
 template <int D, class T, bool JVP>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshView<T> mv, Phys<T> ph,
                                                    const T* __restrict__ W,
@@ -38,6 +48,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshV
                                                    const T* __restrict__ Pf) {
   using S = typename std::conditional<JVP, Dual<T>, T>::type;
   constexpr int M = D + 2, PU = M * (1 + D);
+  constexpr int MP = pad16(M, sizeof(T)), DP = pad16(M * D, sizeof(T));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   const int nb = mv.nb, nm = mv.nm, nqf = mv.nqf, E = mv.E;
@@ -45,42 +56,35 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshV
   const int f0 = blockIdx.x * fpc;
   const int nloc = min(fpc, nfaces - f0);
   if (nloc <= 0) return;
-  // shared layout
-  T* sW = sm;                                   // [fpc][2][nb]
-  T* sV = sW + (size_t)fpc * 2 * nb;            // [fpc][2][nb] (JVP)
-  T* sG = sV + (JVP ? (size_t)fpc * 2 * nb : 0);// [fpc][2][nqf][M]  normal column of K(u)(jump n)
-  T* sF = sG + (size_t)fpc * 2 * nqf * M;       // [fpc][nqf][M]     flux (Roe + avg F_v, + lifting)
-  T* sD = sF + (size_t)fpc * nqf * M;           // [fpc][2][nqf][M][D]  dual tensors / 2
+  const size_t cz = (size_t)fpc * 2 * nm * MP;
+  T* sW = sm;                                   // [fpc][2][nm][MP]
+  T* sV = sW + cz;                              // [fpc][2][nm][MP] (JVP)
+  T* sG = sV + (JVP ? cz : 0);                  // [fpc][2][nqf][MP]
+  T* sF = sG + (size_t)fpc * 2 * nqf * MP;      // [fpc][nqf][MP]
+  T* sD = sF + (size_t)fpc * nqf * MP;          // [fpc][2][nqf][DP]
   // phase 0: stage the modal coefficients of both elements of every face
   for (int t = threadIdx.x; t < nloc * 2 * nb; t += blockDim.x) {
-    int fl = t / (2 * nb), r = t % (2 * nb), side = r / nb, j = r % nb;
-    int f = f0 + fl, k = f / E, e = f % E;
-    int el = side == 0 ? e : mv.nbr[(e * D + k) * 2 + 1];
-    if (!Pf) sW[t] = W[(size_t)el * nb + j];
-    if (JVP) sV[t] = V[(size_t)el * nb + j];
+    const int fl = t / (2 * nb), r = t % (2 * nb), side = r / nb, j = r % nb, v = j / nm, i = j % nm;
+    const int f = f0 + fl, k = f / E, e = f % E;
+    const int el = side == 0 ? e : mv.nbr[(e * D + k) * 2 + 1];
+    const size_t o = ((size_t)(fl * 2 + side) * nm + i) * MP + v;
+    if (!Pf) sW[o] = W[(size_t)el * nb + j];
+    if (JVP) sV[o] = V[(size_t)el * nb + j];
   }
   __syncthreads();
   // phase 1: pointwise physics at the face points (with Pf, a JVP takes the
   // primal traces of both sides from the cache and interpolates only v)
   for (int t = threadIdx.x; t < nloc * nqf; t += blockDim.x) {
-    int fl = t / nqf, q = t % nqf;
-    int f = f0 + fl, k = f / E;
-    int fL = 2 * k + 1, fR = 2 * k;           // local face of L (xi_k = +1) and R (xi_k = -1)
+    const int fl = t / nqf, q = t % nqf;
+    const int f = f0 + fl, k = f / E;
+    const int fL = 2 * k + 1, fR = 2 * k;     // local face of L (xi_k = +1) and R (xi_k = -1)
+    const T* pkL = mv.fpk + ((size_t)fL * nm * nqf + q) * 4;   // mode i at + i * nqf * 4
+    const T* pkR = mv.fpk + ((size_t)fR * nm * nqf + q) * 4;
+    const T* wL = sW + (size_t)fl * 2 * nm * MP;
+    const T* wR = wL + (size_t)nm * MP;
+    const T* vL = sV + (size_t)fl * 2 * nm * MP;
+    const T* vR = vL + (size_t)nm * MP;
     S uL[M], uR[M], gL[M][D], gR[M][D];
-#pragma unroll
-    for (int v = 0; v < M; ++v) {
-      uL[v] = T(0);
-      uR[v] = T(0);
-#pragma unroll
-      for (int kk = 0; kk < D; ++kk) {
-        gL[v][kk] = T(0);
-        gR[v][kk] = T(0);
-      }
-    }
-    const T* wL = sW + (size_t)fl * 2 * nb;
-    const T* wR = wL + nb;
-    const T* vL = sV + (size_t)fl * 2 * nb;
-    const T* vR = vL + nb;
     bool interp = true;
     if constexpr (JVP) {
       if (Pf) {
@@ -93,23 +97,19 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshV
           for (int kk = 0; kk < D; ++kk) hL[v][kk] = hR[v][kk] = T(0);
         }
         for (int i = 0; i < nm; ++i) {
-          const T pL = mv.fphiT[((size_t)fL * nm + i) * nqf + q];
-          const T pR = mv.fphiT[((size_t)fR * nm + i) * nqf + q];
-          T dL[D], dR[D];
-#pragma unroll
-          for (int kk = 0; kk < D; ++kk) {
-            dL[kk] = mv.fdphiT[(((size_t)fL * D + kk) * nm + i) * nqf + q];
-            dR[kk] = mv.fdphiT[(((size_t)fR * D + kk) * nm + i) * nqf + q];
-          }
+          T pL[4], pR[4], a[MP], b[MP];
+          ld_vec<T, 4>(pkL + (size_t)i * nqf * 4, pL);
+          ld_vec<T, 4>(pkR + (size_t)i * nqf * 4, pR);
+          ld_vec<T, MP>(vL + (size_t)i * MP, a);
+          ld_vec<T, MP>(vR + (size_t)i * MP, b);
 #pragma unroll
           for (int v = 0; v < M; ++v) {
-            const T a = vL[v * nm + i], b = vR[v * nm + i];
-            tL[v] += a * pL;
-            tR[v] += b * pR;
+            tL[v] += a[v] * pL[0];
+            tR[v] += b[v] * pR[0];
 #pragma unroll
             for (int kk = 0; kk < D; ++kk) {
-              hL[v][kk] += a * dL[kk];
-              hR[v][kk] += b * dR[kk];
+              hL[v][kk] += a[v] * pL[1 + kk];
+              hR[v][kk] += b[v] * pR[1 + kk];
             }
           }
         }
@@ -127,31 +127,45 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshV
         }
       }
     }
-    for (int i = 0; interp && i < nm; ++i) {
-      T pL = mv.fphiT[((size_t)fL * nm + i) * nqf + q];
-      T pR = mv.fphiT[((size_t)fR * nm + i) * nqf + q];
-      T dL[D], dR[D];
-#pragma unroll
-      for (int kk = 0; kk < D; ++kk) {
-        dL[kk] = mv.fdphiT[(((size_t)fL * D + kk) * nm + i) * nqf + q];
-        dR[kk] = mv.fdphiT[(((size_t)fR * D + kk) * nm + i) * nqf + q];
-      }
+    if (interp) {
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        S a, b;
-        if constexpr (JVP) {
-          a = S(wL[v * nm + i], vL[v * nm + i]);
-          b = S(wR[v * nm + i], vR[v * nm + i]);
-        } else {
-          a = wL[v * nm + i];
-          b = wR[v * nm + i];
-        }
-        uL[v] = uL[v] + a * pL;
-        uR[v] = uR[v] + b * pR;
+        uL[v] = T(0);
+        uR[v] = T(0);
 #pragma unroll
         for (int kk = 0; kk < D; ++kk) {
-          gL[v][kk] = gL[v][kk] + a * dL[kk];
-          gR[v][kk] = gR[v][kk] + b * dR[kk];
+          gL[v][kk] = T(0);
+          gR[v][kk] = T(0);
+        }
+      }
+      for (int i = 0; i < nm; ++i) {
+        T pL[4], pR[4], a0[MP], b0[MP];
+        ld_vec<T, 4>(pkL + (size_t)i * nqf * 4, pL);
+        ld_vec<T, 4>(pkR + (size_t)i * nqf * 4, pR);
+        ld_vec<T, MP>(wL + (size_t)i * MP, a0);
+        ld_vec<T, MP>(wR + (size_t)i * MP, b0);
+        T a1[MP], b1[MP];
+        if constexpr (JVP) {
+          ld_vec<T, MP>(vL + (size_t)i * MP, a1);
+          ld_vec<T, MP>(vR + (size_t)i * MP, b1);
+        }
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+          S a, b;
+          if constexpr (JVP) {
+            a = S(a0[v], a1[v]);
+            b = S(b0[v], b1[v]);
+          } else {
+            a = a0[v];
+            b = b0[v];
+          }
+          uL[v] = uL[v] + a * pL[0];
+          uR[v] = uR[v] + b * pR[0];
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) {
+            gL[v][kk] = gL[v][kk] + a * pL[1 + kk];
+            gR[v][kk] = gR[v][kk] + b * pR[1 + kk];
+          }
         }
       }
     }
@@ -159,11 +173,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshV
       atomicOr(status, ST_NONPHYSICAL);
     S fp[M], GLn[M], GRn[M], DL[M][D], DR[M][D];
     face_point_k<D, S, T>(k, uL, gL, uR, gR, ph, fp, GLn, GRn, DL, DR);
-    T* g0 = sG + ((size_t)fl * 2 * nqf + q) * M;
-    T* g1 = sG + ((size_t)(fl * 2 + 1) * nqf + q) * M;
-    T* fo = sF + ((size_t)fl * nqf + q) * M;
-    T* d0 = sD + (((size_t)fl * 2) * nqf + q) * M * D;
-    T* d1 = sD + (((size_t)fl * 2 + 1) * nqf + q) * M * D;
+    T* g0 = sG + ((size_t)fl * 2 * nqf + q) * MP;
+    T* g1 = sG + ((size_t)(fl * 2 + 1) * nqf + q) * MP;
+    T* fo = sF + ((size_t)fl * nqf + q) * MP;
+    T* d0 = sD + (((size_t)fl * 2) * nqf + q) * DP;
+    T* d1 = sD + (((size_t)fl * 2 + 1) * nqf + q) * DP;
 #pragma unroll
     for (int v = 0; v < M; ++v) {
       fo[v] = JVP ? tan_part(fp[v]) : val(fp[v]);
@@ -179,48 +193,61 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshV
   __syncthreads();
   // phase 2: BR2 lifting on both sides, fhat = Roe + {F_v}.n + eta {delta}.n
   for (int t = threadIdx.x; t < nloc * nqf; t += blockDim.x) {
-    int fl = t / nqf, q = t % nqf;
-    int k = (f0 + fl) / E;
-    const T* PL = mv.lift + ((size_t)(2 * k + 1) * nqf + q) * nqf;
-    const T* PR = mv.lift + ((size_t)(2 * k) * nqf + q) * nqf;
+    const int fl = t / nqf, q = t % nqf;
+    const int k = (f0 + fl) / E;
+    const T* PL = mv.lift + (size_t)(2 * k + 1) * nqf * nqf + q;   // column q2 at PL[q2 * nqf]
+    const T* PR = mv.lift + (size_t)(2 * k) * nqf * nqf + q;
+    const T* gA = sG + (size_t)fl * 2 * nqf * MP;
+    const T* gB = gA + (size_t)nqf * MP;
     T dl[M], dr[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) dl[v] = dr[v] = T(0);
     for (int q2 = 0; q2 < nqf; ++q2) {
-      T a = PL[q2], b = PR[q2];
-      const T* g0 = sG + ((size_t)fl * 2 * nqf + q2) * M;
-      const T* g1 = sG + ((size_t)(fl * 2 + 1) * nqf + q2) * M;
+      const T a = PL[(size_t)q2 * nqf], b = PR[(size_t)q2 * nqf];
+      T ga[MP], gb[MP];
+      ld_vec<T, MP>(gA + (size_t)q2 * MP, ga);
+      ld_vec<T, MP>(gB + (size_t)q2 * MP, gb);
 #pragma unroll
       for (int v = 0; v < M; ++v) {
-        dl[v] += a * g0[v];
-        dr[v] += b * g1[v];
+        dl[v] += a * ga[v];
+        dr[v] += b * gb[v];
       }
     }
-    T* fo = sF + ((size_t)fl * nqf + q) * M;
+    T* fo = sF + ((size_t)fl * nqf + q) * MP;
 #pragma unroll
     for (int v = 0; v < M; ++v) fo[v] += ph.eta * T(0.5) * (dl[v] + dr[v]);
   }
   __syncthreads();
-  // phase 3: projection onto the test functions of both elements
-  for (int t = threadIdx.x; t < nloc * 2 * nb; t += blockDim.x) {
-    int fl = t / (2 * nb), r = t % (2 * nb), side = r / nb, j = r % nb;
-    int v = j / nm, i = j % nm;
-    int f = f0 + fl, k = f / E, e = f % E;
-    int lf = side == 0 ? 2 * k + 1 : 2 * k;
-    T sgn = side == 0 ? T(1) : T(-1);
-    const T* fw = mv.fw + (size_t)k * nqf;
-    const T* ph_ = mv.fphi + (size_t)lf * nqf * nm;
-    const T* dph = mv.fdphi + (size_t)lf * D * nqf * nm;
-    const T* Fo = sF + (size_t)fl * nqf * M;
-    const T* Dd = sD + ((size_t)(fl * 2 + side) * nqf) * M * D;
-    T acc = T(0);
-    for (int q = 0; q < nqf; ++q) {
-      T s = sgn * ph_[(size_t)q * nm + i] * Fo[q * M + v];
+  // phase 3: projection onto the test functions of both elements, a thread per
+  // (face, side, mode) and all M variables
+  for (int t = threadIdx.x; t < nloc * 2 * nm; t += blockDim.x) {
+    const int fl = t / (2 * nm), r = t % (2 * nm), side = r / nm, i = r % nm;
+    const int f = f0 + fl, k = f / E, e = f % E;
+    const int lf = side == 0 ? 2 * k + 1 : 2 * k;
+    const T sgn = side == 0 ? T(1) : T(-1);
+    const T* pw = mv.fpw + ((size_t)lf * nqf * nm + i) * 4;   // point q at + q * nm * 4
+    const T* Fo = sF + (size_t)fl * nqf * MP;
+    const T* Dd = sD + (size_t)(fl * 2 + side) * nqf * DP;
+    T acc[M];
 #pragma unroll
-      for (int kk = 0; kk < D; ++kk) s -= dph[((size_t)kk * nqf + q) * nm + i] * Dd[(q * M + v) * D + kk];
-      acc += fw[q] * s;
+    for (int v = 0; v < M; ++v) acc[v] = T(0);
+    for (int q = 0; q < nqf; ++q) {
+      T w4[4], fq[MP], dq[DP];
+      ld_vec<T, 4>(pw + (size_t)q * nm * 4, w4);
+      ld_vec<T, MP>(Fo + (size_t)q * MP, fq);
+      ld_vec<T, DP>(Dd + (size_t)q * DP, dq);
+      const T sw = sgn * w4[0];
+#pragma unroll
+      for (int v = 0; v < M; ++v) {
+        T s_ = sw * fq[v];
+#pragma unroll
+        for (int kk = 0; kk < D; ++kk) s_ -= w4[1 + kk] * dq[v * D + kk];
+        acc[v] += s_;
+      }
     }
-    slots[(((size_t)e * D + k) * 2 + side) * nb + j] = acc;
+    T* out = slots + (((size_t)e * D + k) * 2 + side) * nb + i;
+#pragma unroll
+    for (int v = 0; v < M; ++v) out[(size_t)v * nm] = acc[v];
   }
 }
 
@@ -311,11 +338,15 @@ __global__ void __launch_bounds__(256) volume_kernel(MeshView<T> mv, Phys<T> ph,
 
 // FP32 volume kernel with the basis tables in shared memory: one persistent
 // CTA per SM stages Tab[0][i][q] = phi_i(q) and Tab[1+k][i][q] = d phi_i/dx_k (q)
-// once (q padded to an odd stride, so that the projection's column reads are
-// free of bank conflicts), then NSLOT independent groups of 256 threads each
-// walk over elements, synchronising only among themselves (named barriers).
-// The same three phases as volume_kernel: interpolation (thread per point),
-// F_c + F_v, projection (thread per (v, i)) plus the face slots.
+// once (q padded to an odd stride, so that the column reads are free of bank
+// conflicts), then NSLOT independent groups of 256 threads each walk over
+// elements, synchronising only among themselves (named barriers).  The same
+// three phases as volume_kernel: interpolation (thread per point, the
+// coefficients mode-major so that one mode's M variables are two 16-byte
+// loads), F_c + F_v (a point's M x D values padded to FP for 16-byte loads),
+// and the projection, where a thread takes one mode i and every NC-th point
+// for all M variables (the point's fluxes read once for M outputs); the NC
+// partial sums of each output are added in a fixed order, with the face slots.
 template <int D, bool JVP, int NSLOT>
 __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<float> mv, Phys<float> ph,
                                                                    const float* __restrict__ W,
@@ -327,11 +358,12 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
   using T = float;
   using S = typename std::conditional<JVP, Dual<T>, T>::type;
   constexpr int M = D + 2, NT = 1 + D, PU = M * (1 + D);
+  constexpr int MP = pad16(M, 4), FP = pad16(M * D, 4);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nb = mv.nb, nm = mv.nm, nq = mv.nq, E = mv.E;
   T* Tab = reinterpret_cast<T*>(smem_raw);            // [1 + D][nm][nqp]
   T* sw = Tab + (size_t)NT * nm * nqp;                 // [nq] weights * |J|
-  const size_t per_slot = (size_t)nb * (JVP ? 2 : 1) + (size_t)nq * M * D;
+  const size_t per_slot = (size_t)nm * MP * (JVP ? 2 : 1) + (size_t)nq * FP;
   for (int t = threadIdx.x; t < NT * nm * nq; t += blockDim.x) {
     const int r = t / nq, q = t - r * nq;               // r = kk * nm + i
     const int kk = r / nm, i = r - kk * nm;
@@ -343,23 +375,20 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
   const int slot = threadIdx.x >> 8, tid = threadIdx.x & 255;
   T* sW = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(sw + nq) + 15) & ~uintptr_t(15)) +
        (size_t)slot * ((per_slot + 3) / 4 * 4);
-  T* sV = sW + nb;
-  T* sF = sV + (JVP ? nb : 0);                          // [nq][M][D]
+  T* sV = sW + (size_t)nm * MP;                         // [nm][MP]
+  T* sF = sV + (JVP ? (size_t)nm * MP : 0);             // [nq][FP]; then the projection's partial sums
+  // projection split: NC point classes per mode, the partials [NC][nb] fit in sF
+  const int NC = max(1, min(min(256 / nm, nq), (int)(((size_t)nq * FP) / nb)));
   const int bar = 1 + slot;
   for (int e = blockIdx.x * NSLOT + slot; e < E; e += gridDim.x * NSLOT) {
     for (int t = tid; t < nb; t += 256) {
-      if (!Pv) sW[t] = W[(size_t)e * nb + t];
-      if (JVP) sV[t] = V[(size_t)e * nb + t];
+      const int v = t / nm, i = t - v * nm;
+      if (!Pv) sW[i * MP + v] = W[(size_t)e * nb + t];
+      if (JVP) sV[i * MP + v] = V[(size_t)e * nb + t];
     }
     asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
     for (int q = tid; q < nq; q += 256) {
       S u[M], g[M][D];
-#pragma unroll
-      for (int v = 0; v < M; ++v) {
-        u[v] = T(0);
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) g[v][kk] = T(0);
-      }
       const T* tq = Tab + q;
       bool interp = true;
       if constexpr (JVP) {
@@ -374,15 +403,15 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
           }
           for (int i = 0; i < nm; ++i) {
             const T p = tq[(size_t)i * nqp];
-            T dp[D];
+            T dp[D], a[MP];
 #pragma unroll
             for (int kk = 0; kk < D; ++kk) dp[kk] = tq[((size_t)(1 + kk) * nm + i) * nqp];
+            ld_vec<T, MP>(sV + (size_t)i * MP, a);
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-              const T a = sV[v * nm + i];
-              tv[v] += a * p;
+              tv[v] += a[v] * p;
 #pragma unroll
-              for (int kk = 0; kk < D; ++kk) th[v][kk] += a * dp[kk];
+              for (int kk = 0; kk < D; ++kk) th[v][kk] += a[v] * dp[kk];
             }
           }
           const T* c = Pv + ((size_t)e * nq + q) * PU;
@@ -394,52 +423,75 @@ __global__ void __launch_bounds__(256 * NSLOT, 1) volume_kernel_st(MeshView<floa
           }
         }
       }
-      for (int i = 0; interp && i < nm; ++i) {
-        const T p = tq[(size_t)i * nqp];
-        T dp[D];
-#pragma unroll
-        for (int kk = 0; kk < D; ++kk) dp[kk] = tq[((size_t)(1 + kk) * nm + i) * nqp];
+      if (interp) {
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-          S a;
-          if constexpr (JVP) a = S(sW[v * nm + i], sV[v * nm + i]);
-          else a = sW[v * nm + i];
-          u[v] = u[v] + a * p;
+          u[v] = T(0);
 #pragma unroll
-          for (int kk = 0; kk < D; ++kk) g[v][kk] = g[v][kk] + a * dp[kk];
+          for (int kk = 0; kk < D; ++kk) g[v][kk] = T(0);
+        }
+        for (int i = 0; i < nm; ++i) {
+          const T p = tq[(size_t)i * nqp];
+          T dp[D], a0[MP], a1[MP];
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) dp[kk] = tq[((size_t)(1 + kk) * nm + i) * nqp];
+          ld_vec<T, MP>(sW + (size_t)i * MP, a0);
+          if constexpr (JVP) ld_vec<T, MP>(sV + (size_t)i * MP, a1);
+#pragma unroll
+          for (int v = 0; v < M; ++v) {
+            S a;
+            if constexpr (JVP) a = S(a0[v], a1[v]);
+            else a = a0[v];
+            u[v] = u[v] + a * p;
+#pragma unroll
+            for (int kk = 0; kk < D; ++kk) g[v][kk] = g[v][kk] + a * dp[kk];
+          }
         }
       }
       if (!physical<D>(u, ph.gm1)) atomicOr(status, ST_NONPHYSICAL);
       S F[M][D];
       flux_total<D, S, T>(u, g, F, ph);
       const T wq = sw[q];
-      T* fo = sF + (size_t)q * M * D;
+      T* fo = sF + (size_t)q * FP;
 #pragma unroll
       for (int v = 0; v < M; ++v)
 #pragma unroll
         for (int kk = 0; kk < D; ++kk) fo[v * D + kk] = wq * (JVP ? tan_part(F[v][kk]) : val(F[v][kk]));
     }
     asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
-    for (int j = tid; j < nb; j += 256) {
-      const int v = j / nm, i = j - v * nm;
-      T acc[D];
+    // projection onto grad phi_i: partial sums over the points q = c, c + NC, ..
+    T acc[M];
+    const int pi = tid % nm, pc = tid / nm;
+    if (pc < NC) {
 #pragma unroll
-      for (int kk = 0; kk < D; ++kk) acc[kk] = T(0);
-      const T* fv = sF + v * D;
-      for (int q = 0; q < nq; ++q) {
+      for (int v = 0; v < M; ++v) acc[v] = T(0);
+      for (int q = pc; q < nq; q += NC) {
+        T dp[D], f[FP];
 #pragma unroll
-        for (int kk = 0; kk < D; ++kk) acc[kk] += Tab[((size_t)(1 + kk) * nm + i) * nqp + q] * fv[(size_t)q * M * D + kk];
+        for (int kk = 0; kk < D; ++kk) dp[kk] = Tab[((size_t)(1 + kk) * nm + pi) * nqp + q];
+        ld_vec<T, FP>(sF + (size_t)q * FP, f);
+#pragma unroll
+        for (int v = 0; v < M; ++v)
+#pragma unroll
+          for (int kk = 0; kk < D; ++kk) acc[v] += dp[kk] * f[v * D + kk];
       }
-      T a = T(0);
+    }
+    asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
+    if (pc < NC) {
 #pragma unroll
-      for (int kk = 0; kk < D; ++kk) a -= acc[kk];
+      for (int v = 0; v < M; ++v) sF[(size_t)pc * nb + v * nm + pi] = acc[v];
+    }
+    asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
+    for (int j = tid; j < nb; j += 256) {
+      T a = T(0);
+      for (int c = 0; c < NC; ++c) a -= sF[(size_t)c * nb + j];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const int em = mv.nbr[(e * D + k) * 2 + 0];
         a += slots[(((size_t)e * D + k) * 2 + 0) * nb + j];
         a += slots[(((size_t)em * D + k) * 2 + 1) * nb + j];
       }
-      if (JVP) a += sigma * mv.detJ * sV[j];
+      if (JVP) a += sigma * mv.detJ * sV[(j % nm) * MP + j / nm];
       else if (Src) a -= Src[(size_t)e * nb + j];
       out[(size_t)e * nb + j] = a;
     }
@@ -453,7 +505,7 @@ constexpr int VOL_SLOTS = 3;
 static bool vol_tables_fit(const Mesh& M, bool jvp, size_t* bytes, int* nqp) {
   if (M.nb > 256) return false;
   *nqp = M.nq | 1;
-  const size_t per_slot = (size_t)M.nb * (jvp ? 2 : 1) + (size_t)M.nq * M.m * M.d;
+  const size_t per_slot = (size_t)M.nm * pad16(M.m, 4) * (jvp ? 2 : 1) + (size_t)M.nq * pad16(M.m * M.d, 4);
   const size_t n = (size_t)(1 + M.d) * M.nm * *nqp + M.nq;
   *bytes = n * sizeof(float) + 16 + VOL_SLOTS * ((per_slot + 3) / 4 * 4) * sizeof(float);
   int dev = 0, smax = 0;
@@ -464,8 +516,8 @@ static bool vol_tables_fit(const Mesh& M, bool jvp, size_t* bytes, int* nqp) {
 
 template <class T>
 static size_t face_smem(const Mesh& M, int fpc, bool jvp) {
-  return sizeof(T) * (size_t)fpc *
-         (2 * M.nb * (jvp ? 2 : 1) + 2 * M.nqf * M.m + M.nqf * M.m + 2 * M.nqf * M.m * M.d);
+  const size_t MP = pad16(M.m, sizeof(T)), DP = pad16(M.m * M.d, sizeof(T));
+  return sizeof(T) * (size_t)fpc * (2 * M.nm * MP * (jvp ? 2 : 1) + 2 * M.nqf * MP + M.nqf * MP + 2 * M.nqf * DP);
 }
 template <class T>
 static size_t vol_smem(const Mesh& M, int epc, bool jvp) {
@@ -486,13 +538,14 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
   int nfaces = D * Ms.E;
   if (parts & 1) {
     // 3-D: the face term by sum factorisation in FP64 (fewer of the FP64 pipe's
-    // cycles: the residual 4.5 -> 3.8 ms at 16^3 p = 4) and in FP32 above 40
-    // modes (at p = 4 the direct FP32 kernel is faster: 0.39 against 0.57 ms);
-    // DG_NO_SUMFACT_FACE=1 keeps the direct kernel, DG_SUMFACT_FACE_MIN_MODES
-    // moves the FP32 threshold (41 modes)
+    // cycles: the residual 4.4 -> 3.8 ms at 16^3 p = 4, 125 -> 73 ms at 32^3
+    // p = 6); in FP32 the direct kernel is faster (smoother JVP 0.23 against
+    // 0.56 ms at p = 4, 4.9 against 9.1 ms at p = 6).  DG_NO_SUMFACT_FACE=1
+    // keeps the direct kernel; DG_SUMFACT_FACE_MIN_MODES=n takes the sum-
+    // factorised one in FP32 from n modes on
     const char* nsff = getenv("DG_NO_SUMFACT_FACE");
     const char* sfmin = getenv("DG_SUMFACT_FACE_MIN_MODES");
-    const int min_modes = sfmin ? atoi(sfmin) : 41;
+    const int min_modes = sfmin ? atoi(sfmin) : INT_MAX;
     cudaError_t e = cudaErrorNotSupported;
     if (D == 3 && !(nsff && nsff[0] == '1') && (std::is_same<T, double>::value || Ms.nm >= min_modes)) {
       e = launch_face_sf<T>(Ms, W, V, slots, JVP, JVP ? Pf : nullptr, st);

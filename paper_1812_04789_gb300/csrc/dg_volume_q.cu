@@ -29,9 +29,15 @@ namespace {
 
 struct QPlan {
   int n1, nq, nt, nqd;
-  size_t oL, oW, oS, oF, total;   // element offsets in shared memory (T)
+  size_t oL, oW, oZ, oY, oF, oP, total;   // element offsets in shared memory (T)
 };
 
+__host__ __device__ constexpr size_t zmax(size_t a, size_t b) { return a > b ? a : b; }
+
+// 3-D: two regions, each holding in turn what is live at that stage:
+//   A: Z (interpolation), then F (pointwise fluxes), then R (modes)
+//   B: the coefficients W, then Y (interpolation), then P, Q (projection)
+// 2-D: W, the stages (Y, then P) and F apart.
 template <int D>
 __host__ __device__ inline QPlan q_plan(int p, int nq, int M, bool jvp) {
   QPlan P;
@@ -43,24 +49,28 @@ __host__ __device__ inline QPlan q_plan(int p, int nq, int M, bool jvp) {
     P.nt *= P.n1;
     P.nqd *= nq;
   }
-  const int nc = jvp ? 2 : 1;   // value (+ tangent) copies
+  const size_t nc = jvp ? 2 : 1;   // value (+ tangent) copies
+  const size_t n1 = P.n1;
   size_t o = 0;
   P.oL = o;
-  o += (size_t)2 * P.n1 * nq + nq;
-  P.oW = o;
-  o += (size_t)nc * M * P.nt;
-  P.oS = o;   // interpolation stages, later reused by the projection stages
-  size_t interp, proj;
+  o += 2 * n1 * nq + nq;
   if (D == 3) {
-    interp = (size_t)nc * (2 * M * P.n1 * P.n1 * nq + 3 * M * P.n1 * nq * nq);
-    proj = (size_t)3 * M * P.n1 * nq * nq + 2 * M * P.n1 * P.n1 * nq;
+    const size_t nZ = 2 * M * n1 * n1 * nq, nY = 3 * M * n1 * nq * nq;
+    const size_t nP = M * n1 * nq * nq, nQ = M * n1 * n1 * nq;
+    const size_t A = zmax(nc * nZ, (size_t)D * M * P.nqd);
+    const size_t B = zmax(zmax(nc * M * P.nt, nc * nY), 3 * nP + 2 * nQ);
+    P.oZ = P.oF = o;
+    o += A;
+    P.oW = P.oY = P.oP = o;
+    o += B;
   } else {
-    interp = (size_t)nc * 2 * M * P.n1 * nq;
-    proj = (size_t)2 * M * P.n1 * nq;
+    P.oW = o;
+    o += nc * M * P.nt;
+    P.oY = P.oP = P.oZ = o;
+    o += zmax(nc * 2 * M * n1 * nq, (size_t)2 * M * n1 * nq);
+    P.oF = o;
+    o += (size_t)D * M * P.nqd;
   }
-  o += std::max(interp, proj);
-  P.oF = o;
-  o += (size_t)D * M * P.nqd;
   P.total = o;
   return P;
 }
@@ -81,7 +91,6 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
   const T* dL = L + n1 * nq;         // dL[a][q]
   const T* w1 = dL + n1 * nq;        // w[q]
   T* Wt = sm + P.oW;                 // [c][v][t], c = value, tangent
-  T* St = sm + P.oS;
   T* F = sm + P.oF;                  // [k][v][q]: w_q |J| F (value or tangent)
   const T met[3] = {m0, m1, m2};
   for (int t = threadIdx.x; t < 2 * n1 * nq + nq; t += blockDim.x) sm[P.oL + t] = l1g[t];
@@ -95,8 +104,8 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
     // ---------------- interpolation
     if (D == 3) {
       const int nZ = 2 * M * n1 * n1 * nq, nY = 3 * M * n1 * nq * nq;
-      T* Z = St;              // [c][s][v][a0][a1][q2]
-      T* Y = St + NC * nZ;    // [c][t][v][a0][q1][q2]
+      T* Z = sm + P.oZ;       // [c][s][v][a0][a1][q2]
+      T* Y = sm + P.oY;       // [c][t][v][a0][q1][q2] (over W: Z is complete)
       for (int t = threadIdx.x; t < NC * nZ; t += blockDim.x) {
         const int c = t / nZ, r = t - c * nZ;
         const int q2 = r % nq, a1 = (r / nq) % n1, a0 = (r / (nq * n1)) % n1, v = (r / (nq * n1 * n1)) % M,
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
       }
     } else {
       const int nY = 2 * M * n1 * nq;
-      T* Y = St;   // [c][s][v][a0][q1]
+      T* Y = sm + P.oY;   // [c][s][v][a0][q1]
       for (int t = threadIdx.x; t < NC * nY; t += blockDim.x) {
         const int c = t / nY, r = t - c * nY;
         const int q1 = r % nq, a0 = (r / nq) % n1, v = (r / (nq * n1)) % M, s = r / (nq * n1 * M);
@@ -149,7 +158,7 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
         }
         if (D == 3) {
           const int nY = 3 * M * n1 * nq * nq;
-          const T* Y = St + NC * 2 * M * n1 * n1 * nq;
+          const T* Y = sm + P.oY;
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
             const T* y0 = Y + (size_t)c * nY + ((size_t)(0 * M + v) * n1) * nq * nq + yq;
@@ -168,8 +177,8 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
           const int nY = 2 * M * n1 * nq;
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const T* y0 = St + (size_t)c * nY + ((size_t)(0 * M + v) * n1) * nq + yq;
-            const T* y1 = St + (size_t)c * nY + ((size_t)(1 * M + v) * n1) * nq + yq;
+            const T* y0 = sm + P.oY + (size_t)c * nY + ((size_t)(0 * M + v) * n1) * nq + yq;
+            const T* y1 = sm + P.oY + (size_t)c * nY + ((size_t)(1 * M + v) * n1) * nq + yq;
             for (int a0 = 0; a0 < n1; ++a0) {
               const T la = L[a0 * nq + q0], da = dL[a0 * nq + q0];
               const T v0 = y0[a0 * nq];
@@ -209,8 +218,8 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
     T* R = nullptr;   // [v][t] in the last stage's buffer
     if (D == 3) {
       const int nP = M * n1 * nq * nq, nQ = M * n1 * n1 * nq;
-      T* Pb = St;             // [j][v][a0][q1][q2]
-      T* Qb = St + 3 * nP;    // [A, B][v][a0][a1][q2]
+      T* Pb = sm + P.oP;      // [j][v][a0][q1][q2] (over Y: F is complete)
+      T* Qb = Pb + 3 * nP;    // [A, B][v][a0][a1][q2]
       for (int t = threadIdx.x; t < 3 * nP; t += blockDim.x) {
         const int j = t / nP, r = t - j * nP;
         const int q12 = r % (nq * nq), a0 = (r / (nq * nq)) % n1, v = r / (nq * nq * n1);
@@ -249,7 +258,7 @@ __global__ void __launch_bounds__(256) volume_q_kernel(MeshView<T> mv, Phys<T> p
       }
     } else {
       const int nP = M * n1 * nq;
-      T* Pb = St;   // [j][v][a0][q1]
+      T* Pb = sm + P.oP;   // [j][v][a0][q1]
       for (int t = threadIdx.x; t < 2 * nP; t += blockDim.x) {
         const int j = t / nP, r = t - j * nP;
         const int q1 = r % nq, a0 = (r / nq) % n1, v = r / (nq * n1);

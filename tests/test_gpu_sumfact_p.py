@@ -70,8 +70,9 @@ def test_sumfact_p6_fp32_jvp_vs_oracle(monkeypatch):
 @pytest.mark.parametrize("space", ["P", "Q"])
 @pytest.mark.parametrize("n,p", [((3, 4, 2), 1), ((1, 3, 2), 3), ((4, 3, 3), 4), ((2, 2, 3), 6)])
 def test_sumfact_faces_equal_direct_kernel(n, p, space, monkeypatch):
-    """The face term by sum factorisation (3-D; FP64, and FP32 above 40 modes)
-    against the direct face kernel (DG_NO_SUMFACT_FACE=1): residual and JVP in
+    """The face term by sum factorisation (3-D; FP64 by default, FP32 here too
+    through DG_SUMFACT_FACE_MIN_MODES=1) against the direct face kernel
+    (DG_NO_SUMFACT_FACE=1): residual and JVP in
     FP64 to 1e-13, the FP32 JVP mode to 2e-5 (both relative max-norm), and the
     FP64 result against the oracle to 1e-12; a direction with one element
     makes an element its own face neighbour."""
@@ -82,6 +83,7 @@ def test_sumfact_faces_equal_direct_kernel(n, p, space, monkeypatch):
     v = wl.random_vector(W.shape, 10)
     sigma = 2.5
     out = {}
+    monkeypatch.setenv("DG_SUMFACT_FACE_MIN_MODES", "1")
     for flag in ("0", "1"):
         monkeypatch.setenv("DG_NO_SUMFACT_FACE", flag)
         R, K = _eval(cfg, W, v, sigma, B.JVP_EXACT)
