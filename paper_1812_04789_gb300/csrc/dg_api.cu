@@ -265,7 +265,7 @@ static dg_status alloc_mg(dg_pmg h, MG<T>& mg) {
       CK(plan_coop_smoother(bf16 ? 1 : 0, L.nb, M.nfaces(), M.E, nmax, &L.coop));
       if (L.coop.ok) {
         L.coop.nu_max = nmax;
-        CK(dalloc(mg.allocs, (void**)&L.cpart, sizeof(double) * (size_t)L.coop.grid * (2 * (nmax + 1) + 1),
+        CK(dalloc(mg.allocs, (void**)&L.cpart, sizeof(double) * (size_t)(L.coop.grid + 1) * (2 * (nmax + 1) + 1),
                   &h->vector_bytes));
         CK(dalloc(mg.allocs, (void**)&L.cbar, sizeof(unsigned) * COOP_BAR_WORDS, &h->vector_bytes));
       }

@@ -322,7 +322,7 @@ struct Level {
   unsigned short* Dop16 = nullptr;
   unsigned short* O16 = nullptr;
   CoopPlan coop;             // persistent smoother (FP32 coarse levels), when available
-  double* cpart = nullptr;   //   its reduction partials
+  double* cpart = nullptr;   //   its reduction partials [grid][2 (nu + 1) + 1], then the totals
   unsigned* cbar = nullptr;  //   and barrier counter
 };
 

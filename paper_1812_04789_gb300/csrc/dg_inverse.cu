@@ -76,15 +76,16 @@ __global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict
       }
     unsigned used = 0;   // bit a: row ty + 16 a has been a pivot row
     bool bad = false;
-    for (int k = 0; k < nb; ++k) {
-      const int kx = k & 15, kb = k >> 4;
+    // k = 16 kb + kx: the register column kb is a compile-time index (the
+    // unrolled kb loop), so reading and rewriting column k needs no selects
+#pragma unroll
+    for (int kb = 0; kb < R; ++kb)
+    for (int kx = 0; kx < 16; ++kx) {
+      const int k = 16 * kb + kx;
+      if (k >= nb) break;
       T col[R];
 #pragma unroll
-      for (int b = 0; b < R; ++b)
-        if (b == kb) {
-#pragma unroll
-          for (int a = 0; a < R; ++a) col[a] = t[a][b];
-        }
+      for (int a = 0; a < R; ++a) col[a] = t[a][kb];
       if (tx == kx) {   // the 16 owners of column k: best unused row of their R
         T best = T(-1), sv = T(0);
         int bi = INT_MAX;
@@ -173,14 +174,10 @@ __global__ void __launch_bounds__(256, 1) block_inverse_reg_kernel(T* __restrict
       }
       if (tx == kx) {
 #pragma unroll
-        for (int b = 0; b < R; ++b)
-          if (b == kb) {
-#pragma unroll
-            for (int a = 0; a < R; ++a) {
-              const int i = ty + 16 * a;
-              t[a][b] = (i == p) ? ipiv : -ck[a] * ipiv;
-            }
-          }
+        for (int a = 0; a < R; ++a) {
+          const int i = ty + 16 * a;
+          t[a][kb] = (i == p) ? ipiv : -ck[a] * ipiv;
+        }
       }
     }
     __syncthreads();   // piv_row / step_of complete

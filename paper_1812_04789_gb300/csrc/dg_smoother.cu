@@ -19,14 +19,17 @@
 // Swirydowicz et al. 2021, which saves a barrier: h2 is at rounding level
 // against w, so the difference loses nothing.  Where it would cancel, more
 // than 99 % of ||w||^2, the norm is summed explicitly behind a fourth
-// barrier; every CTA takes the same branch.)  Every CTA sums the partials
-// of all CTAs in the same fixed order and keeps its own copy of the
+// barrier; every CTA takes the same branch.)  A barrier that ends a
+// reduction also sums it: the last CTA to arrive adds the CTAs' partials in a
+// fixed order (FP64) and publishes the sums before it releases the others,
+// which then read only the sums.  Every CTA keeps its own copy of the
 // Hessenberg matrix, the Givens rotations and g, so all CTAs hold identical
-// scalars and the final x += Z y needs no further barrier.  The per-row
-// arithmetic is FP32 (products, w -= V h with h rounded to FP32, x += Z y):
-// GB300 runs FP64 and FP32<->FP64 conversions at a small fraction of its FP32
-// rate, and per-row FP64 made the smoother FP64-bound; only the sums across
-// rows, warps and CTAs are FP64.
+// scalars and the final x += Z y needs no further barrier.  The arithmetic
+// inside a CTA is FP32 (products and their sums over the CTA's rows, w -= V h
+// with h rounded to FP32, the Givens rotations and the small least-squares
+// solve, x += Z y): GB300 runs FP64 and FP32<->FP64 conversions at a small
+// fraction of its FP32 rate, with long latencies, and FP64 there made the
+// smoother FP64-bound; only the sums across CTAs are FP64.
 //
 // The grid barrier counts arrivals in one word and releases the waiting CTAs
 // through another (its own 128-byte line, so the polls do not contend with
@@ -72,7 +75,7 @@ struct CoopArgs {
   const float* b;
   float* x;
   float* Z;             // nu x N: the directions z_j, read by the neighbours' products
-  double* part;         // [grid][2 (nu + 1) + 1]
+  double* part;         // [grid][2 (nu + 1) + 1] partials, then one row of sums
   unsigned* bar;        // [0]: arrivals, [32]: released barrier number; zero at launch
   int* status;          // mesh status word (ST_TIMEOUT)
   int* kflag;           // Krylov status bits (ST_NONFINITE)
@@ -121,63 +124,112 @@ __device__ bool grid_barrier(unsigned* bar, unsigned k, unsigned expect, int* st
   return *sflag != 0;
 }
 
-// sum over the CTA's threads of s, valid in every thread (red: 32 doubles)
-__device__ double block_sum(double s, double* red) {
+// Grid barrier number k that also sums the CTAs' partials: the last CTA to
+// arrive adds part[c * stride + off + i] over c = 0..G-1 for i < nv (16 lanes
+// per value, each lane its c = lane, lane + 16, .. loaded at once and summed as
+// a tree, then a butterfly: the same order whichever CTA is last) into tot[i], then releases the
+// others; every CTA copies tot[0, nv) into dst (shared memory).  One CTA reads
+// the G x nv partials instead of every CTA.  False when a wait ran out here or
+// elsewhere (ST_TIMEOUT), and then the caller returns.
+__device__ bool grid_barrier_sum(unsigned* bar, unsigned k, unsigned expect, int* status, int* sflag,
+                                 const double* part, int stride, int off, int nv, int G, double* tot,
+                                 double* dst) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned old = atomicAdd(bar, 1u);
+    __threadfence();
+    sflag[2] = old + 1u == k * expect ? 1 : 0;
+  }
+  __syncthreads();
+  if (sflag[2]) {
+    const int grp = threadIdx.x >> 4, l16 = threadIdx.x & 15, ngrp = blockDim.x >> 4;
+    for (int i0 = 0; i0 < nv; i0 += ngrp) {
+      const int i = i0 + grp;   // uniform per 16-lane group
+      // every load of a lane issued at once (12 per lane: G <= 192 in one
+      // round trip), summed as a tree
+      double t[12];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int u = 0; u < 12; ++u) {
+        const int c = l16 + 16 * u;
+        t[u] = (i < nv && c < G) ? __ldcg(part + (size_t)c * stride + off + i) : 0.0;
+      }
+      double s = (((t[0] + t[1]) + (t[2] + t[3])) + ((t[4] + t[5]) + (t[6] + t[7]))) +
+                 ((t[8] + t[9]) + (t[10] + t[11]));
+      for (int c = l16 + 192; i < nv && c < G; c += 16) s += __ldcg(part + (size_t)c * stride + off + i);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (i < nv && l16 == 0) tot[i] = s;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicExch(bar + 32, k);            // release barrier k
+      sflag[0] = 1;
+    }
+  } else if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned long long t0 = global_ns();
+    while (*(volatile unsigned*)(bar + 32) < k) {
+      if (*(volatile int*)status & ST_TIMEOUT) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > 2000000000ull) {
+        atomicOr(status, ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(20);
+    }
+    __threadfence();
+    sflag[0] = ok;
+  }
   __syncthreads();
-  if (lane == 0) red[warp] = s;
+  if (!sflag[0]) return false;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = __ldcg(tot + i);
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-  return t;
+  return true;
+}
+
+// FP32 sum over the CTA's threads of f (warp butterflies, then warp 0 over
+// the warp sums), valid in every thread; redf: 33 floats, [32] the result
+__device__ float block_sum_f(float f, float* redf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();   // earlier readers of redf are done
+  if (lane == 0) redf[warp] = f;
+  __syncthreads();
+  if (warp == 0) {
+    float t = lane < nw ? redf[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) redf[32] = t;
+  }
+  __syncthreads();
+  return redf[32];
 }
 
 // out[i] = sum over the CTA's rows of V_i . w (shared memory), i < nv, warp per
-// i; FP32 products summed 16 at a time, then in FP64
+// i, in FP32 (a lane's rows, then the warp's butterfly); the CTA partials are
+// then summed across CTAs in FP64
 __device__ void own_dots(int nv, const float* Vs, int ldv, const float* ws, int rows, double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i < nv; i += nw) {
     const float* v = Vs + (size_t)i * ldv;
-    double s = 0.0;
-    for (int r0 = lane; r0 < rows; r0 += 16 * 32) {
-      float f = 0.f;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int r = r0 + 32 * u;
-        if (r < rows) f = fmaf(v[r], ws[r], f);
-      }
-      s += (double)f;
+    float f0 = 0.f, f1 = 0.f;
+    int r = lane;
+    for (; r + 32 < rows; r += 64) {
+      f0 = fmaf(v[r], ws[r], f0);
+      f1 = fmaf(v[r + 32], ws[r + 32], f1);
     }
+    if (r < rows) f0 = fmaf(v[r], ws[r], f0);
+    float f = f0 + f1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[i] = s;
+    for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+    if (lane == 0) out[i] = (double)f;
   }
-}
-
-// dst[i] = sum over CTAs c = 0..G-1 of part[c * stride + i], i < nv, in a
-// fixed order (the same in every CTA); other CTAs' partials read past L1,
-// eight loads in flight per lane
-__device__ void sum_parts(int nv, const double* part, int stride, int G, double* dst) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < nv; i += nw) {
-    double s = 0.0;
-    for (int c0 = lane; c0 < G; c0 += 8 * 32) {
-      double t[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int c = c0 + 32 * u;
-        t[u] = c < G ? __ldcg(part + (size_t)c * stride + i) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) s += t[u];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) dst[i] = s;
-  }
-  __syncthreads();
 }
 
 // ws[own rows of e] = [b_e -] (D_e in_e + sum_s O_{e,s} in_nbr(e,s)) for the
@@ -272,23 +324,25 @@ template <class S, int NF>
 __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nu = a.nu, ldh = nu + 1, nb = a.nb;
-  double* H = reinterpret_cast<double*>(smem_raw);   // (nu + 1) x nu, column-major
-  double* cs = H + (size_t)ldh * nu;
-  double* sn = cs + nu;
-  double* g = sn + nu;                                // nu + 1
-  double* h1 = g + ldh;                               // nu + 1
-  double* h2 = h1 + ldh;                              // nu + 1
-  double* red = h2 + ldh;                             // 32
-  int* sflag = reinterpret_cast<int*>(red + 32);      // 4 ints
+  double* h1 = reinterpret_cast<double*>(smem_raw);   // nu + 1: first-pass coefficients (FP64 sums)
+  double* h2 = h1 + ldh;                              // nu + 2: second pass, then ||w||^2
+  double* hx = h2 + ldh + 1;                          // 2: broadcast scalars
+  int* sflag = reinterpret_cast<int*>(hx + 2);        // 4 ints
+  float* H = reinterpret_cast<float*>(sflag + 4);     // (nu + 1) x nu, column-major
+  float* cs = H + (size_t)ldh * nu;
+  float* sn = cs + nu;
+  float* g = sn + nu;                                 // nu + 1
+  float* hf = g + ldh;                                // nu + 1: coefficients rounded to FP32, then y
+  float* redf = hf + ldh;                             // 33
   const int rmax = a.chunk * nb;
-  float* hf = reinterpret_cast<float*>(sflag + 4);    // [nu + 1] coefficients rounded to FP32
-  float* Vs = hf + ((ldh + 3) & ~3);                  // [nu + 1][rmax]
+  float* Vs = redf + ((33 + 3) & ~3);                 // [nu + 1][rmax]
   float* Zs = Vs + (size_t)ldh * rmax;                // [nu][rmax]
   float* ws = Zs + (size_t)nu * rmax;                 // [rmax]
   float* xs = ws + rmax;                              // [epc][1 + nf][nb]
 
   const int G = gridDim.x, stride = 2 * ldh + 1;
   double* mypart = a.part + (size_t)blockIdx.x * stride;   // [0, ldh): pass 1, [ldh, 2 ldh): pass 2, last: norm
+  double* tot = a.part + (size_t)G * stride;               // the sums, written by the last CTA of a barrier
   const int e_beg = min(a.E, (int)blockIdx.x * a.chunk), ne = min(a.E, e_beg + a.chunk) - e_beg;
   const int rows = ne * nb;
   const long N = a.N;
@@ -304,26 +358,21 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
   {
     float f = 0.f;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) f = fmaf(ws[r], ws[r], f);
-    const double s = block_sum((double)f, red);
-    if (threadIdx.x == 0) mypart[2 * ldh] = s;
+    const float s = block_sum_f(f, redf);
+    if (threadIdx.x == 0) mypart[2 * ldh] = (double)s;
   }
-  if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
-  sum_parts(1, a.part + 2 * ldh, stride, G, h2);
+  if (!grid_barrier_sum(a.bar, ++nbar, expect, a.status, sflag, a.part, stride, 2 * ldh, 1, G, tot, h2)) return;
   const double beta = sqrt(h2[0]);
   if (!(beta > 0.0) || !isfinite(beta)) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && !isfinite(beta)) atomicOr(a.kflag, ST_NONFINITE);
     return;   // b - A x = 0 (or not finite): nothing to smooth
   }
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < ldh; ++i) g[i] = 0.0;
-    g[0] = beta;
-  }
-  double inv = 1.0 / beta;
+  for (int i = threadIdx.x; i < ldh; i += blockDim.x) g[i] = i == 0 ? (float)beta : 0.f;
+  float finv = (float)(1.0 / beta);
   int kdone = 0;
   for (int j = 0; j < nu; ++j) {
     // A: v_j = w / ||w||, z_j = D^{-1} v_j
     float* vj = Vs + (size_t)j * rmax;
-    const float finv = (float)inv;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) vj[r] = finv * ws[r];
     __syncthreads();
     float* zg = a.Z + (size_t)j * N;
@@ -332,9 +381,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
     // B: w = A z_j, first pass of inner products
     bsr_own<S, NF>(a, zg, nullptr, ws, e_beg, ne, xs);
     own_dots(j + 1, Vs, rmax, ws, rows, mypart);
-    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
+    if (!grid_barrier_sum(a.bar, ++nbar, expect, a.status, sflag, a.part, stride, 0, j + 1, G, tot, h1)) return;
     // C: w -= V h1; second pass of inner products and ||w||^2 (at mypart[ldh + j + 1])
-    sum_parts(j + 1, a.part, stride, G, h1);
     if (threadIdx.x <= j) hf[threadIdx.x] = (float)h1[threadIdx.x];
     __syncthreads();
     {
@@ -345,21 +393,30 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
         ws[r] = acc;
         f = fmaf(acc, acc, f);
       }
-      const double s = block_sum((double)f, red);
+      const float s = block_sum_f(f, redf);
       own_dots(j + 1, Vs, rmax, ws, rows, mypart + ldh);
-      if (threadIdx.x == 0) mypart[ldh + j + 1] = s;
+      if (threadIdx.x == 0) mypart[ldh + j + 1] = (double)s;
     }
-    if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
-    // D: w -= V h2, ||w - V h2|| from ||w||^2 - ||h2||^2
-    sum_parts(j + 2, a.part + ldh, stride, G, h2);   // h2[j + 1] = ||w||^2
-    if (threadIdx.x == 0) {
-      double hs = 0.0;
-      for (int i = 0; i <= j; ++i) hs += h2[i] * h2[i];
-      red[17] = h2[j + 1] - hs;
+    if (!grid_barrier_sum(a.bar, ++nbar, expect, a.status, sflag, a.part, stride, ldh, j + 2, G, tot, h2))
+      return;   // h2[j + 1] = ||w||^2
+    // D: w -= V h2, ||w - V h2|| from ||w||^2 - ||h2||^2; Hessenberg column j
+    // (h1 + h2, formed in parallel) in FP32
+    if (threadIdx.x <= j) {
+      hf[threadIdx.x] = (float)h2[threadIdx.x];
+      H[(size_t)j * ldh + threadIdx.x] = (float)(h1[threadIdx.x] + h2[threadIdx.x]);
     }
-    if (threadIdx.x <= j) hf[threadIdx.x] = (float)h2[threadIdx.x];
+    if (threadIdx.x < 32) {   // ||h2||^2 (FP32: h2 is at rounding level against ||w||)
+      float q = 0.f;
+      for (int i = threadIdx.x; i <= j; i += 32) {
+        const float t = (float)h2[i];
+        q = fmaf(t, t, q);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (threadIdx.x == 0) hx[0] = h2[j + 1] - (double)q;
+    }
     __syncthreads();
-    const double nw2 = h2[j + 1], hn2 = red[17];
+    const double nw2 = h2[j + 1], hn2 = hx[0];
     const bool explicit_norm = !(hn2 >= 0.01 * nw2);   // cancellation (or not finite): sum it
     {
       float f = 0.f;
@@ -370,39 +427,38 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
         f = fmaf(acc, acc, f);
       }
       if (explicit_norm) {
-        const double s = block_sum((double)f, red);
-        if (threadIdx.x == 0) mypart[2 * ldh] = s;
+        const float s = block_sum_f(f, redf);
+        if (threadIdx.x == 0) mypart[2 * ldh] = (double)s;
       }
     }
     double hn;
     if (explicit_norm) {
-      if (!grid_barrier(a.bar, ++nbar, expect, a.status, sflag)) return;
-      sum_parts(1, a.part + 2 * ldh, stride, G, red + 16);   // red[16] = ||w||^2 (red[0..15] free here)
-      hn = sqrt(red[16]);
+      if (!grid_barrier_sum(a.bar, ++nbar, expect, a.status, sflag, a.part, stride, 2 * ldh, 1, G, tot, hx + 1))
+        return;
+      hn = sqrt(hx[1]);
     } else {
       hn = sqrt(hn2);
     }
-    // Hessenberg column j, earlier rotations, new rotation, g (every CTA alike)
+    // earlier rotations, new rotation, g (every CTA alike, FP32)
     if (threadIdx.x == 0) {
-      double* h = H + (size_t)j * ldh;
-      for (int i = 0; i <= j; ++i) h[i] = h1[i] + h2[i];
-      h[j + 1] = hn;
+      float* h = H + (size_t)j * ldh;
+      h[j + 1] = (float)hn;
       for (int i = 0; i < j; ++i) {
-        const double p = h[i], q = h[i + 1];
+        const float p = h[i], q = h[i + 1];
         h[i] = cs[i] * p + sn[i] * q;
         h[i + 1] = -sn[i] * p + cs[i] * q;
       }
-      const double p = h[j], q = h[j + 1];
-      const double rr = hypot(p, q);
-      double c = 1.0, sv = 0.0;
-      if (rr != 0.0) {
+      const float p = h[j], q = h[j + 1];
+      const float rr = hypotf(p, q);
+      float c = 1.f, sv = 0.f;
+      if (rr != 0.f) {
         c = p / rr;
         sv = q / rr;
       }
       cs[j] = c;
       sn[j] = sv;
       h[j] = c * p + sv * q;
-      h[j + 1] = 0.0;
+      h[j + 1] = 0.f;
       g[j + 1] = -sv * g[j];
       g[j] = c * g[j];
     }
@@ -412,16 +468,15 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
       if (threadIdx.x == 0 && blockIdx.x == 0 && !isfinite(hn)) atomicOr(a.kflag, ST_NONFINITE);
       break;
     }
-    inv = 1.0 / hn;
+    finv = (float)(1.0 / hn);
   }
-  // y = H[:k,:k]^{-1} g[:k] (back substitution, into h1), x += Z y on own rows
+  // y = H[:k,:k]^{-1} g[:k] (back substitution, FP32, into hf), x += Z y on own rows
   if (threadIdx.x == 0) {
     for (int i = kdone - 1; i >= 0; --i) {
-      double s = g[i];
-      for (int c = i + 1; c < kdone; ++c) s -= H[(size_t)c * ldh + i] * h1[c];
-      const double d = H[(size_t)i * ldh + i];
-      h1[i] = d != 0.0 ? s / d : 0.0;
-      hf[i] = (float)h1[i];
+      float s = g[i];
+      for (int c = i + 1; c < kdone; ++c) s -= H[(size_t)c * ldh + i] * hf[c];
+      const float d = H[(size_t)i * ldh + i];
+      hf[i] = d != 0.f ? s / d : 0.f;
     }
   }
   __syncthreads();
@@ -435,10 +490,11 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) coop_smooth_kernel(CoopArgs<S
 
 static size_t coop_smem(int nu, int nb, int nf, int chunk, int epc) {
   const size_t ldh = nu + 1;
-  const size_t dbl = ldh * nu + 2 * (size_t)nu + 3 * ldh + 32;
+  const size_t dbl = 2 * ldh + 1 + 2;
+  const size_t fsc = ldh * nu + 2 * (size_t)nu + 2 * ldh + 36;   // H, cs, sn, g, hf, redf (padded)
   const size_t rmax = (size_t)chunk * nb;
-  const size_t flt = ((ldh + 3) & ~(size_t)3) + (2 * (size_t)nu + 2) * rmax + (size_t)epc * (1 + nf) * nb;
-  return dbl * sizeof(double) + 4 * sizeof(int) + flt * sizeof(float);
+  const size_t flt = (2 * (size_t)nu + 2) * rmax + (size_t)epc * (1 + nf) * nb;
+  return dbl * sizeof(double) + 4 * sizeof(int) + (fsc + flt) * sizeof(float) + 16;
 }
 
 template <class S, int NF>
