@@ -43,7 +43,8 @@ namespace dgk {
 
 namespace {
 
-constexpr int TC_THREADS = 256;
+constexpr int TC_PROD = 256;                // operand producers (8 warps)
+constexpr int TC_THREADS = TC_PROD + 32;    // + one warp whose lane 0 issues the MMAs
 constexpr int TC_MAX_TILES = 8;
 constexpr int TC_TMEM_COLS = 512;
 constexpr long long TC_WAIT_LIMIT = 4000000000LL;   // SM cycles (about 2 s)
@@ -196,9 +197,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     probe_stage_primal<D, float>(mv, ph, W, e, nbrs, cW, cU, cFU, true, status);
     for (int g = 0; g < P.ngroups; ++g) {
       const int w0 = g * G, Gc = min(G, M - w0);
-      const int npair = Gc * M, tpw = TC_THREADS / npair, rows = npair * nm;
+      const int npair = Gc * M, tpw = TC_PROD / npair, rows = npair * nm;
       const int tilesG = (rows + 127) >> 7;
       int ks = 0;
+      // K step whose operands are complete but whose MMAs are not issued yet
+      // (-1: none); warp TC_PROD / 32 (not a producer) issues them
+      int pend = -1;
+      auto issue_pending = [&]() {
+        if (pend < 0) return;
+        const int pb = pend & 1;
+        if (threadIdx.x == TC_PROD) {
+          fence_after_sync();
+          const float* Ab = A + pb * bufA;
+          const float* Bb = Bs + pb * bufB;
+          const uint64_t bh = desc_kmajor(smem_u32(Bb)), bl = desc_kmajor(smem_u32(Bb + npad * 8));
+#pragma unroll 1
+          for (int pass = 0; pass < 3; ++pass) {
+            const float* Ap = Ab + (pass == 2 ? tiles * 1024 : 0);
+            const uint64_t bd = pass == 1 ? bl : bh;
+#pragma unroll 1
+            for (int ti = 0; ti < tilesG; ++ti)
+              mma_tf32(tmem + (uint32_t)(ti * npad), desc_kmajor(smem_u32(Ap + ti * 1024)), bd, idesc,
+                       pend > 0 || pass > 0);
+          }
+          commit(&mbar[pb]);
+        }
+        ++issued[pb];
+        pend = -1;
+      };
+      // the B operand (bufB / 4 <= 4 npad <= 1024 float4) of the next K step, in registers
+      constexpr int BPRE = (4 * 256 + TC_THREADS - 1) / TC_THREADS;
+      float4 bpre[BPRE];
+#pragma unroll
+      for (int u = 0; u < BPRE; ++u) {
+        const int t = threadIdx.x + u * TC_THREADS;
+        bpre[u] = t < bufB / 4 ? reinterpret_cast<const float4*>(trial)[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       for (int part = 0; part < 2; ++part) {
         const int npts = part == 0 ? P.npv : NF * nqf, ubase = part == 0 ? 0 : P.npv;
         for (int c0 = 0; c0 < npts; c0 += jq) {
@@ -269,7 +303,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           for (int kk = 0; kk < ncj / 2; ++kk, ++ks) {
             const int b = ks & 1;
             bool late = false;
-            if (issued[b] > waited[b]) {   // the MMAs that last read buffer b
+            if (issued[b] > waited[b]) {   // the MMAs that last read buffer b (K step ks - 2)
               if (mbar_wait(&mbar[b], (issued[b] - 1u) & 1u, TC_WAIT_LIMIT))
                 waited[b] = issued[b];
               else
@@ -281,10 +315,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
               goto done;
             }
-            {
-              const float4* src = reinterpret_cast<const float4*>(trial + (size_t)((ubase + c0) / 2 + kk) * bufB);
-              float4* dst = reinterpret_cast<float4*>(Bs + b * bufB);
-              for (int t = threadIdx.x; t < bufB / 4; t += blockDim.x) dst[t] = src[t];
+            issue_pending();   // K step ks - 1 (its operands complete at the barrier above)
+#pragma unroll
+            for (int u = 0; u < BPRE; ++u) {   // B of this step from registers, then prefetch the next
+              const int t = threadIdx.x + u * TC_THREADS;
+              if (t < bufB / 4) {
+                reinterpret_cast<float4*>(Bs + b * bufB)[t] = bpre[u];
+                if (ks + 1 < P.nks) bpre[u] = reinterpret_cast<const float4*>(trial + (size_t)(ks + 1) * bufB)[t];
+              }
             }
             if ((int)threadIdx.x < npair * tpw) {
               const int pair = threadIdx.x / tpw, i0 = threadIdx.x % tpw;
@@ -297,25 +335,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         nm, nmp);
             }
             fence_proxy_async();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-              fence_after_sync();
-              const float* Ab = A + b * bufA;
-              const float* Bb = Bs + b * bufB;
-              const uint64_t bh = desc_kmajor(smem_u32(Bb)), bl = desc_kmajor(smem_u32(Bb + npad * 8));
-#pragma unroll 1
-              for (int pass = 0; pass < 3; ++pass) {
-                const float* Ap = Ab + (pass == 2 ? tiles * 1024 : 0);
-                const uint64_t bd = pass == 1 ? bl : bh;
-#pragma unroll 1
-                for (int ti = 0; ti < tilesG; ++ti)
-                  mma_tf32(tmem + (uint32_t)(ti * npad), desc_kmajor(smem_u32(Ap + ti * 1024)), bd, idesc,
-                           ks > 0 || pass > 0);
-              }
-              commit(&mbar[b]);
-            }
-            ++issued[b];
+            pend = ks;
           }
+          // the chunk's last operands are complete and Jb / Ts may be refilled
+          // once every producer is here; its MMAs run during the next J stage
+          __syncthreads();
+          issue_pending();
         }
       }
       {   // drain, then the epilogue: TMEM -> block rows (v, i'), columns (w, i)
@@ -333,7 +358,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         fence_after_sync();
         const int lb = (warp & 3) * 32;
-        for (int ti = warp >> 2; ti < tilesG; ti += TC_THREADS / 128) {
+        for (int ti = warp >> 2; warp < TC_PROD / 32 && ti < tilesG; ti += TC_PROD / 128) {
           const int r = ti * 128 + lb + lane;
           for (int c0 = 0; c0 < nm; c0 += 16) {
             float v16[16];
