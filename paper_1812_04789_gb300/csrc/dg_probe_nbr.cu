@@ -13,7 +13,7 @@
 // table) and TrialN the neighbour's basis on its face.  Per face and chunk of
 // points: (J) one dual-number evaluation per (point, w, s'), (Z) the test side
 // contracted first, Z[(w,v,i'), (q,s')] = sum_c Test J, (O) O += Z TrialN,
-// written to the block in global memory (the first chunk stores, later ones add).
+// summed in registers over the face's chunks and written to the block once.
 // Faces of a direction with a single element are not handled here (they feed
 // the diagonal block; the SIMT probe covers that case).
 #include <algorithm>
@@ -25,6 +25,7 @@ namespace dgk {
 namespace {
 
 constexpr int NBR_THREADS = 256;
+constexpr int NBR_ACC = 10;   // block entries a thread holds in registers across a face's point chunks
 
 struct NbrPlan {
   int ok = 0, jq = 0, oFU = 0, oJ = 0, oT = 0, oN = 0, oZ = 0, smem = 0;
@@ -60,7 +61,7 @@ NbrPlan nbr_plan(int d, int nm, int nqf, int nmc, int smax) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> mv, Phys<float> ph,
+__global__ void __launch_bounds__(NBR_THREADS, 1) probe_nbr_kernel(MeshView<float> mv, Phys<float> ph,
                                                                 const float* __restrict__ W,
                                                                 float* __restrict__ Oout, int nmc, int ldo,
                                                                 const float* __restrict__ test, int npv,
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> 
     for (int s = 0; s < NF; ++s) {
       T* Os = Oout + ((size_t)e * NF + s) * ostride;
       const int f = s ^ 1;   // the neighbour's local face
+      T oacc[NBR_ACC];
       for (int q0 = 0; q0 < nqf; q0 += jq) {
         const int ncj = min(jq, nqf - q0);
         // (J) neighbour-seeded tangents of the face-point outputs
@@ -151,8 +153,24 @@ __global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> 
           }
         }
         __syncthreads();
-        // (O) trial side, into the block
-        for (int t = threadIdx.x; t < R * nmc; t += blockDim.x) {
+        // (O) trial side: a thread's entries t = threadIdx.x + u * blockDim.x
+        // accumulate in registers over the face's chunks (or, for blocks with
+        // more than NBR_ACC * blockDim.x entries, in the block in global memory)
+#pragma unroll
+        for (int u = 0; u < NBR_ACC; ++u) {
+          const int t = threadIdx.x + u * blockDim.x;
+          if (t < R * nmc) {
+            const int row = t / nmc, i = t - row * nmc;
+            T a = T(0);
+            for (int pl = 0; pl < ncj; ++pl) {
+              const float4 z = *reinterpret_cast<const float4*>(Zs + ((size_t)pl * R + row) * 4);
+              const T* tn = Tn + (size_t)pl * 4 * nmc + i;
+              a += z.x * tn[0] + z.y * tn[nmc] + z.z * tn[2 * nmc] + z.w * tn[3 * nmc];
+            }
+            oacc[u] = q0 == 0 ? a : oacc[u] + a;
+          }
+        }
+        for (int t = threadIdx.x + NBR_ACC * blockDim.x; t < R * nmc; t += blockDim.x) {
           const int row = t / nmc, i = t - row * nmc;
           const int w = row / nbc, v = (row / nmc) % M, ip = row % nmc;
           T acc = T(0);
@@ -167,6 +185,18 @@ __global__ void __launch_bounds__(NBR_THREADS) probe_nbr_kernel(MeshView<float> 
           *o = q0 == 0 ? acc : *o + acc;
         }
         __syncthreads();
+      }
+      // the register-held entries of the face's block, written once
+#pragma unroll
+      for (int u = 0; u < NBR_ACC; ++u) {
+        const int t = threadIdx.x + u * blockDim.x;
+        if (t < R * nmc) {
+          const int row = t / nmc, i = t - row * nmc;
+          const int w = row / nbc, v = (row / nmc) % M, ip = row % nmc;
+          T* o = ldo > 0 ? Os + (size_t)(w * nmc + i) * ldo + v * nmc + ip
+                         : Os + (size_t)(v * nmc + ip) * nbc + w * nmc + i;
+          *o = oacc[u];
+        }
       }
     }
   }

@@ -43,8 +43,9 @@ namespace dgk {
 
 namespace {
 
-constexpr int TC_PROD = 256;                // operand producers (8 warps)
-constexpr int TC_THREADS = TC_PROD + 32;    // + one warp whose lane 0 issues the MMAs
+constexpr int TC_PROD = 256;                        // operand producers (8 warps)
+constexpr int TC_ISSUERS = 2;                       // warps whose lane 0 issues MMAs (alternate tiles)
+constexpr int TC_THREADS = TC_PROD + 32 * TC_ISSUERS;
 constexpr int TC_MAX_TILES = 8;
 constexpr int TC_TMEM_COLS = 512;
 constexpr long long TC_WAIT_LIMIT = 4000000000LL;   // SM cycles (about 2 s)
@@ -176,8 +177,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const float sdj = sigma * mv.detJ;
 
   if (threadIdx.x == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[0], TC_ISSUERS);   // one commit per issuing thread
+    mbar_init(&mbar[1], TC_ISSUERS);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(tslot, (uint32_t)P.tmem_cols);
@@ -201,24 +202,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int tilesG = (rows + 127) >> 7;
       int ks = 0;
       // K step whose operands are complete but whose MMAs are not issued yet
-      // (-1: none); warp TC_PROD / 32 (not a producer) issues them
+      // (-1: none); lane 0 of each of the TC_ISSUERS warps after the producers
+      // issues them for the tiles ti = its index (mod TC_ISSUERS), each tile's
+      // three passes in order (hi.hi, hi.lo, lo.hi), and commits once
       int pend = -1;
       auto issue_pending = [&]() {
         if (pend < 0) return;
         const int pb = pend & 1;
-        if (threadIdx.x == TC_PROD) {
+        const int is = ((int)threadIdx.x - TC_PROD) >> 5;
+        if ((int)threadIdx.x >= TC_PROD && (threadIdx.x & 31) == 0) {
           fence_after_sync();
           const float* Ab = A + pb * bufA;
           const float* Bb = Bs + pb * bufB;
           const uint64_t bh = desc_kmajor(smem_u32(Bb)), bl = desc_kmajor(smem_u32(Bb + npad * 8));
 #pragma unroll 1
-          for (int pass = 0; pass < 3; ++pass) {
-            const float* Ap = Ab + (pass == 2 ? tiles * 1024 : 0);
-            const uint64_t bd = pass == 1 ? bl : bh;
-#pragma unroll 1
-            for (int ti = 0; ti < tilesG; ++ti)
-              mma_tf32(tmem + (uint32_t)(ti * npad), desc_kmajor(smem_u32(Ap + ti * 1024)), bd, idesc,
-                       pend > 0 || pass > 0);
+          for (int ti = is; ti < tilesG; ti += TC_ISSUERS) {
+            const uint64_t ahi = desc_kmajor(smem_u32(Ab + ti * 1024));
+            const uint64_t alo = desc_kmajor(smem_u32(Ab + tiles * 1024 + ti * 1024));
+            const uint32_t d = tmem + (uint32_t)(ti * npad);
+            mma_tf32(d, ahi, bh, idesc, pend > 0);
+            mma_tf32(d, ahi, bl, idesc, true);
+            mma_tf32(d, alo, bh, idesc, true);
           }
           commit(&mbar[pb]);
         }
