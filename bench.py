@@ -31,6 +31,7 @@ import numpy as np  # noqa: E402
 from paper_1812_04789_gb300 import workloads as wl  # noqa: E402
 
 BJ_KERNEL_VERSION = "colmajor-v1"   # bump when the block-Jacobi apply kernel changes
+COOP_KERNEL_VERSION = "coop-fp32-3bar"   # bump when the persistent smoother kernel changes
 METRIC = "Implicit-step DOFs/s (mixed vs FP64, 1 GB300); JVP % HBM roofline; p99 latency"
 UNIT = "DOFs/s"
 
@@ -529,9 +530,17 @@ def kernel_rooflines(torch, B, mixed, fp64, stream, peaks, ref_cfg):
         ms = mixed.pmg.kernel_time(B.KT_SMOOTH, 1, 5, stream=stream)
         nf = 2 * len(mixed.cfg["n"])
         by = E * nb1 * ld1 * 4 * ((nu + 1) * (1 + nf) + nu) + E * nb1 * 4 * (4 + 2 * nu)
+        # DRAM bytes of one such call from a committed ncu capture of the same
+        # configuration and kernel version (profiles/roofline_traffic.json)
+        traffic = None
+        tf = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+        if os.path.exists(tf):
+            rec = json.load(open(tf)).get("coop_level1_mixed", {})
+            if rec.get("config") == ref_cfg and rec.get("kernel_version") == COOP_KERNEL_VERSION:
+                traffic = rec.get("dram_bytes_per_launch")
         out.append({"kernel": "coop_smooth_kernel<float,6> (one smoother call, level 1, %d iterations)" % nu,
                     "bound": "hbm", "dtype": "f32", "achieved": by / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": by / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                    "unit": "GB/s", "frac": by / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": traffic,
                     "ms": ms, "algorithmic_bytes": by})
     return out
 
