@@ -41,7 +41,7 @@ __device__ __forceinline__ int dof(int nm, int v, int i) {
 // fpw with the face weight folded in for the projection), so a mode costs one
 // 16-byte table load per side.
 template <int D, class T, bool JVP>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) face_kernel(MeshView<T> mv, Phys<T> ph,
+__global__ void __launch_bounds__(sizeof(T) == 4 ? 256 : 128, sizeof(T) == 4 ? 2 : 1) face_kernel(MeshView<T> mv, Phys<T> ph,
                                                    const T* __restrict__ W,
                                                    const T* __restrict__ V,
                                                    T* __restrict__ slots, int* status, int fpc,
@@ -530,7 +530,12 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
   MeshView<T> mv = Ms.view<T>();
   Phys<T> ph = Ms.phys_t<T>();
   T* slots = std::is_same<T, double>::value ? (T*)Ms.t64.slots : (T*)Ms.t32.slots;
-  int fpc = std::max(1, 128 / Ms.nqf);
+  // FP32: 256 threads over 256 / n_qf faces (7 at p = 4: 252 of 256 threads busy per point
+  // phase, against 108 of 128 with 3 faces), two CTAs per SM at 128 registers, when two
+  // such CTAs fit shared memory (not for the 125 modes of Q_4: then 128 threads)
+  int fthreads = 128;
+  if (sizeof(T) == 4 && face_smem<T>(Ms, std::max(1, 256 / Ms.nqf), JVP) <= 100 * 1024) fthreads = 256;
+  int fpc = std::max(1, fthreads / Ms.nqf);
   size_t fsm = face_smem<T>(Ms, fpc, JVP);
   while (fsm > 200 * 1024 && fpc > 1) fsm = face_smem<T>(Ms, --fpc, JVP);
   if (fsm > 48 * 1024)
@@ -553,7 +558,7 @@ static cudaError_t run_residual(const Mesh& Ms, const T* W, const T* V, const T*
     }
     if (e == cudaErrorNotSupported) {
       note_launch();
-      face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, 128, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc,
+      face_kernel<D, T, JVP><<<(nfaces + fpc - 1) / fpc, fthreads, fsm, st>>>(mv, ph, W, V, slots, Ms.status, fpc,
                                                                         JVP ? Pf : nullptr);
       e = cudaGetLastError();
     }
