@@ -13,8 +13,9 @@
 // CTAs in FP64: GB300 executes FP64 (and FP32<->FP64 conversions) at a small
 // fraction of its FP32 rate, so a per-entry FP64 multiply-add made these
 // kernels FP64-bound.  The inner products sum at most 16 FP32 products per
-// thread before an FP64 add; the coefficients of w -= V c and x += Z y are
-// rounded to FP32 once per CTA.  Classical Gram-Schmidt applied twice keeps
+// thread before an FP64 add, and a CTA's threads in FP32 (one FP64 partial per
+// CTA, the partials summed in FP64); the coefficients of w -= V c and x += Z y
+// are rounded to FP32 once per CTA.  Classical Gram-Schmidt applied twice keeps
 // the basis orthogonal to working precision with FP32 subtraction: the second
 // pass removes what the rounding of the first left along V.
 #include <math.h>
@@ -141,7 +142,10 @@ template <>
 __global__ void __launch_bounds__(256) mdot_kernel<float>(const float* __restrict__ V, long N,
                                                           const float* __restrict__ w, int G,
                                                           double* __restrict__ part) {
-  __shared__ double red[256];
+  // the CTA's sum in FP32 (a thread's products 16 at a time into FP64, then warp
+  // butterflies and the eight warp sums in FP32: FP64 adds have long latencies
+  // here), one FP64 partial per CTA; the CTAs' partials are summed in FP64
+  __shared__ float red[8];
   const int i = blockIdx.y, c = blockIdx.x;
   const long chunk = (N + G - 1) / G;
   const long beg = c * chunk, end = min(N, beg + chunk);
@@ -156,13 +160,16 @@ __global__ void __launch_bounds__(256) mdot_kernel<float>(const float* __restric
     }
     s += (double)f;
   }
-  red[threadIdx.x] = s;
+  float t = (float)s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
   __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b += red[k];
+    part[(size_t)i * G + c] = (double)b;
   }
-  if (threadIdx.x == 0) part[(size_t)i * G + c] = red[0];
 }
 
 // mode 0: H[i][j] = sum; mode 1: H[i][j] += sum;  (one warp per i, fixed order)
