@@ -451,19 +451,41 @@ __global__ void __launch_bounds__(256) block_inverse_panel_kernel(T* __restrict_
           Pn[(size_t)p * BP + cc] = cc == c ? ipiv : Pn[(size_t)p * BP + cc] * ipiv;
         __syncthreads();
       }
-      // every other column: x <- x + sum_c (X_c - e_{p_c}) x[p_c], a thread per column
+      // every other column: x <- x + sum_c (X_c - e_{p_c}) x[p_c], a thread per column:
+      // the panel rows X[i][0..BP) in 16-byte loads, then the e_{p_c} terms on the
+      // panel's pivot rows (distinct rows, one subtraction each)
       for (int j = threadIdx.x; j < nb; j += blockDim.x) {
         if (j >= k0 && j < k0 + bw) continue;
         T xp[BP];
 #pragma unroll
         for (int c = 0; c < BP; ++c) xp[c] = c < bw ? A[(size_t)pr[c] * nb + j] : T(0);
-        for (int i = 0; i < nb; ++i) {
-          const T* pi = Pn + (size_t)i * BP;
+        // eight rows' loads in flight before their updates
+        int i = 0;
+        for (; i + 8 <= nb; i += 8) {
+          T a[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) a[u] = A[(size_t)(i + u) * nb + j];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            T pi[BP];
+            ld_vec<T, BP>(Pn + (size_t)(i + u) * BP, pi);
+            T acc = a[u];
+#pragma unroll
+            for (int c = 0; c < BP; ++c) acc += pi[c] * xp[c];
+            A[(size_t)(i + u) * nb + j] = acc;
+          }
+        }
+        for (; i < nb; ++i) {
+          T pi[BP];
+          ld_vec<T, BP>(Pn + (size_t)i * BP, pi);
           T acc = A[(size_t)i * nb + j];
 #pragma unroll
-          for (int c = 0; c < BP; ++c) acc += (pi[c] - (i == pr[c] ? T(1) : T(0))) * xp[c];
+          for (int c = 0; c < BP; ++c) acc += pi[c] * xp[c];
           A[(size_t)i * nb + j] = acc;
         }
+#pragma unroll
+        for (int c = 0; c < BP; ++c)
+          if (c < bw) A[(size_t)pr[c] * nb + j] -= xp[c];
       }
       for (int t = threadIdx.x; t < nb * bw; t += blockDim.x) {
         const int i = t / bw, c = t - i * bw;
